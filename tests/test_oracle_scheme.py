@@ -1,0 +1,261 @@
+"""Pins of the oracle's whole MUSCL-Hancock / HLLD / constrained-transport step.
+
+What fixes the expected values:
+  * the exact Riemann solution for Sod (Sec. 3.1, Fig. 7);
+  * conservation of mass, momentum and energy to roundoff in periodic boxes (Sec. 2.1);
+  * the discrete face divergence kept at its initial value (constrained transport, Eq. 12);
+  * the point symmetry of the Orszag-Tang vortex (Sec. 3.1);
+  * second-order convergence on smooth linear waves, whose exact solution is the
+    translated initial profile;
+  * free-stream preservation, exact slopes on linear data, exact edge averages of
+    Eqs. 8-11 on bilinear data;
+  * independence of the result from how the box is cut into patches (the guard fill);
+  * closed-form CFL steps of uniform states.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact_riemann as ER
+from oracle import mhd
+from paper_2508_09568_gb300 import workloads as W
+
+G53 = 5.0 / 3.0
+
+
+def run(geom, U, gamma, limiter=0, **kw):
+    flat = W.to_patches(U, geom)
+    B = mhd.Bunch(geom, gamma, courant=kw.pop("courant", 0.8), limiter=limiter)
+    P = B.split(flat)
+    P, t, k = B.run(P, **kw)
+    return W.from_patches(B.join(P), geom), t, k
+
+
+def divb(G, dx):
+    d = (np.roll(G[5], -1, 2) - G[5]) / dx[0] + (np.roll(G[6], -1, 1) - G[6]) / dx[1] \
+        + (np.roll(G[7], -1, 0) - G[7]) / dx[2]
+    return d
+
+
+# --------------------------------------------------------------------------------------
+# Sod shock tube against the exact solution
+# --------------------------------------------------------------------------------------
+
+def sod_errors(N):
+    geom, U, meta = W.sod(ncell=N, npatch=16)
+    Gs, t, k = run(geom, U, meta["gamma"], t_end=0.2)
+    assert abs(t - 0.2) < 1e-14
+    rho, u = Gs[0, 0, 0], Gs[1, 0, 0] / Gs[0, 0, 0]
+    xl = np.arange(N) / N
+    r, ue, pe = ER.cell_average(xl, xl + 1.0 / N, 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1), 1.4)
+    return np.abs(rho - r).mean(), np.abs(u - ue).mean()
+
+
+def test_sod_matches_exact_and_converges():
+    e = [sod_errors(N) for N in (64, 128, 256)]
+    assert e[2][0] < 4e-3 and e[2][1] < 6e-3
+    assert e[0][0] > e[1][0] > e[2][0]
+    assert e[0][1] > e[1][1] > e[2][1]
+
+
+# --------------------------------------------------------------------------------------
+# invariants
+# --------------------------------------------------------------------------------------
+
+def test_conservation_and_divb_3d():
+    geom, U, meta = W.small_box()
+    G0 = U
+    assert np.max(np.abs(divb(G0, geom.dx))) * geom.dx[0] < 1e-14
+    Gs, t, k = run(geom, U, meta["gamma"], nsteps=12)
+    assert np.all(np.isfinite(Gs))
+    for v in range(5):
+        rel = abs(Gs[v].sum() - G0[v].sum()) / np.abs(G0[v]).sum()
+        assert rel < 1e-13, (v, rel)
+    brms = np.sqrt((Gs[5:8] ** 2).mean())
+    assert np.max(np.abs(divb(Gs, geom.dx))) * geom.dx[0] / brms < 1e-13
+
+
+def test_orszag_tang_symmetry_conservation_divb():
+    geom, U, meta = W.orszag_tang(ncell=48, patch=16)
+    Gs, t, k = run(geom, U, meta["gamma"], t_end=0.5)
+    r = Gs[0, 0]
+    assert np.max(np.abs(r - r[::-1, ::-1])) / r.max() < 1e-10
+    u = Gs[1, 0] / Gs[0, 0]
+    assert np.max(np.abs(u + u[::-1, ::-1])) < 1e-10
+    bx = Gs[5, 0]   # face x_{i-1/2} maps to face x_{N-i+1/2} = index N-i
+    assert np.max(np.abs(bx + np.roll(bx[::-1, ::-1], 1, axis=1))) < 1e-10
+    for v in (0, 4):
+        assert abs(Gs[v].sum() - U[v].sum()) / U[v].sum() < 1e-13
+    brms = np.sqrt((Gs[5:8] ** 2).mean())
+    assert np.max(np.abs(divb(Gs, geom.dx))) * geom.dx[0] / brms < 1e-13
+
+
+# --------------------------------------------------------------------------------------
+# convergence on smooth linear waves
+# --------------------------------------------------------------------------------------
+
+def wave1d(N, kind, limiter, A=1e-6):
+    geom = W.uniform_geometry([N, 1, 1], [N // 4, 1, 1], dx=[1.0 / N, 1.0, 1.0])
+    x = (np.arange(N) + 0.5) / N
+    s = A * np.sin(2 * np.pi * x)[None, None, :]
+    one, zero = np.ones_like(s), np.zeros_like(s)
+    if kind == "alfven":     # Bx = 1, rho = 1: right-going Alfven wave, dv_y = -dB_y
+        U = W.conserved_from_setup(one, (zero, -s, zero), one, (one, s, zero), G53)
+        T, comp = 1.0, 6
+    else:                    # B = 0: right-going sound wave
+        c = math.sqrt(G53)
+        U = W.conserved_from_setup(one + s, (c * s, zero, zero), one + c * c * s, (zero, zero, zero), G53)
+        T, comp = 1.0 / c, 0
+    Gs, t, k = run(geom, U, G53, limiter=limiter, t_end=T)
+    return np.abs(Gs[comp] - U[comp]).mean() / A
+
+
+@pytest.mark.parametrize("kind,limiter,order", [("sound", 0, 1.7), ("sound", 1, 1.9),
+                                                ("alfven", 0, 1.6), ("alfven", 1, 1.9)])
+def test_convergence_order_1d(kind, limiter, order):
+    e = [wave1d(N, kind, limiter) for N in (32, 64, 128)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(rates) >= order, rates
+
+
+def wave2d(N, limiter, A=1e-6):
+    """Oblique (45 degree) Alfven wave in a periodic square, field perturbation in plane
+    built as the discrete curl of an edge potential (so div B = 0 exactly)."""
+    geom = W.uniform_geometry([N, N, 1], [N // 2, N // 2, 1], dx=[1.0 / N, 1.0 / N, 1.0])
+    xc, xf = (np.arange(N) + 0.5) / N, np.arange(N) / N
+    Xc, Yc = np.meshgrid(xc, xc, indexing="xy")
+    Xe, Ye = np.meshgrid(xf, xf, indexing="xy")
+    Az = A / (2 * np.pi * math.sqrt(2)) * np.cos(2 * np.pi * (Xe + Ye))
+    h = 1.0 / N
+    bx = (np.roll(Az, -1, 0) - Az) / h + 1 / math.sqrt(2)
+    by = -(np.roll(Az, -1, 1) - Az) / h + 1 / math.sqrt(2)
+    s = A * np.sin(2 * np.pi * (Xc + Yc))
+    one = np.ones_like(s)[None]
+    U = W.conserved_from_setup(one, ((s / math.sqrt(2))[None], (-s / math.sqrt(2))[None], 0 * one), one,
+                               (bx[None], by[None], 0 * one), G53)
+    Gs, t, k = run(geom, U, G53, limiter=limiter, t_end=1 / math.sqrt(2))
+    return np.abs(Gs[5] - U[5]).mean() / A
+
+
+def test_convergence_order_2d_oblique_alfven():
+    e = [wave2d(N, 1) for N in (16, 32, 64)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(rates) >= 1.7, rates
+
+
+# --------------------------------------------------------------------------------------
+# stencil exactness and free streaming
+# --------------------------------------------------------------------------------------
+
+def test_free_stream_preserved():
+    geom = W.uniform_geometry([12, 12, 12], [6, 6, 6], dx=[1 / 12, 1 / 10, 1 / 8])
+    sh = (12, 12, 12)
+    U = W.conserved_from_setup(np.full(sh, 1.3), (np.full(sh, 0.4), np.full(sh, -0.7), np.full(sh, 0.2)),
+                               np.full(sh, 0.9), (np.full(sh, 0.3), np.full(sh, -0.5), np.full(sh, 0.8)), G53)
+    Gs, t, k = run(geom, U, G53, nsteps=3)
+    assert np.max(np.abs(Gs - U)) < 1e-13
+
+
+def test_slopes_exact_on_linear_data():
+    x = torch.arange(10, dtype=torch.float64)
+    q = (2.5 * x - 1.0).reshape(1, 1, 1, 10)
+    for lim in (mhd.LIMITER_MINMOD, mhd.LIMITER_MC):
+        s = mhd.limited(q, 0, lim)[..., 1:-1]
+        assert torch.all(s == 2.5)
+    # extremum -> zero slope
+    q = torch.tensor([0.0, 1.0, 0.0]).reshape(1, 1, 1, 3).to(torch.float64)
+    assert float(mhd.limited(q, 0, 0)[..., 1]) == 0.0
+
+
+def test_edge_average_exact_on_bilinear_data():
+    """Eqs. 8-11: the 4-cell / 2-face averages reproduce bilinear fields at the edge."""
+    N = 8
+    i = torch.arange(N, dtype=torch.float64)
+    J, I = torch.meshgrid(i, i, indexing="ij")
+    f = lambda x, y: 0.3 + 1.7 * x - 0.9 * y + 0.25 * x * y
+    vx = f(I + 0.5, J + 0.5)[None, None]   # cell centres
+    avg = 0.25 * (vx + mhd.m(vx, 0) + mhd.m(vx, 1) + mhd.m(mhd.m(vx, 0), 1))
+    assert torch.allclose(avg[..., 1:, 1:], f(I, J)[None, None][..., 1:, 1:], atol=1e-13)
+    bx = f(I, J + 0.5)[None, None]        # x-faces
+    avg2 = 0.5 * (bx + mhd.m(bx, 1))
+    assert torch.allclose(avg2[..., 1:, :], f(I, J)[None, None][..., 1:, :], atol=1e-13)
+
+
+# --------------------------------------------------------------------------------------
+# guard fill and patch decomposition
+# --------------------------------------------------------------------------------------
+
+def test_guard_fill_periodic_and_outflow():
+    geom = W.uniform_geometry([12, 8, 1], [4, 4, 1], dx=[1 / 12, 1 / 8, 1],
+                              bc=[[W.BC_OUTFLOW, W.BC_OUTFLOW], [W.BC_PERIODIC] * 2, [W.BC_PERIODIC] * 2])
+    rng = np.random.default_rng(3)
+    Gl = rng.normal(size=(8, 1, 8, 12))
+    flat = W.to_patches(Gl, geom)
+    B = mhd.Bunch(geom, G53)
+    P = B.fill_guards(B.split(flat))
+    # reference: pad the global field (edge copy in x, wrap in y) and cut
+    pad = np.pad(Gl, ((0, 0), (0, 0), (3, 3), (0, 0)), mode="wrap")
+    pad = np.pad(pad, ((0, 0), (0, 0), (0, 0), (3, 3)), mode="edge")
+    for i in range(geom.npatch):
+        o = geom.origin[i]
+        ref = pad[:, :, o[1]:o[1] + 10, o[0]:o[0] + 10]
+        assert np.array_equal(P[i].numpy(), ref)
+
+
+def test_patch_decomposition_is_bitwise_invariant():
+    geom1, U, meta = W.small_box(ncell=(16, 16, 16), patch=(16, 16, 16), seed=11)
+    geom8 = W.uniform_geometry([16] * 3, [8] * 3, dx=geom1.dx)
+    geom_mixed = W.Geometry([[8, 16, 16], [8, 16, 16]], [[0, 0, 0], [8, 0, 0]], [16] * 3, geom1.dx,
+                            [[0, 0]] * 3)
+    outs = [run(g, U, meta["gamma"], nsteps=3)[0] for g in (geom1, geom8, geom_mixed)]
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_result_ignores_unused_ghosts():
+    """The update reads two ghost layers (plus the far face of the normal field)."""
+    geom, U, meta = W.small_box(ncell=(8, 8, 8), patch=(8, 8, 8), seed=5)
+    flat = W.to_patches(U, geom)
+    B = mhd.Bunch(geom, meta["gamma"])
+    Pf = B.fill_guards(B.split(flat))[0][None]
+    out1 = mhd.step(Pf, 1e-3, geom.active, geom.dx, meta["gamma"])
+    Pg = Pf.clone()
+    Pg[..., :, :, 0] = 7.0     # outermost low x layer: all variables
+    Pg[..., :, 0, :] = 7.0
+    Pg[..., 0, :, :] = 7.0
+    Pg[:, :5, :, :, -1] = 7.0  # outermost high x layer: cell-centred variables only
+    Pg[:, :5, :, -1, :] = 7.0
+    Pg[:, :5, -1, :, :] = 7.0
+    out2 = mhd.step(Pg, 1e-3, geom.active, geom.dx, meta["gamma"])
+    sl = (slice(None), slice(None), slice(3, 11), slice(3, 11), slice(3, 11))
+    assert torch.equal(out1[sl], out2[sl])
+
+
+# --------------------------------------------------------------------------------------
+# CFL time step
+# --------------------------------------------------------------------------------------
+
+def test_cfl_dt_closed_form():
+    geom = W.uniform_geometry([8, 8, 8], [4, 4, 4], dx=[0.1, 0.2, 0.25])
+    sh = (8, 8, 8)
+    rho, P, u = 1.2, 0.8, (0.3, -0.4, 0.1)
+    b = (0.5, 0.0, 0.0)
+    U = W.conserved_from_setup(np.full(sh, rho), tuple(np.full(sh, a) for a in u), np.full(sh, P),
+                               tuple(np.full(sh, a) for a in b), G53)
+    B = mhd.Bunch(geom, G53, courant=0.8)
+    P_ = B.fill_guards(B.split(W.to_patches(U, geom)))
+    cs2, ca2 = G53 * P / rho, 0.25 / rho
+    cx = math.sqrt(max(cs2, ca2))             # field along x
+    cyz = math.sqrt(cs2 + ca2)                # field across y and z
+    rate = (0.3 + cx) / 0.1 + (0.4 + cyz) / 0.2 + (0.1 + cyz) / 0.25
+    assert math.isclose(B.cfl_dt(P_), 0.8 / rate, rel_tol=1e-14)
+
+
+def test_cfl_dt_ignores_collapsed_axes():
+    geom, U, meta = W.sod(ncell=64, npatch=4)
+    B = mhd.Bunch(geom, 1.4, courant=0.8)
+    P_ = B.fill_guards(B.split(W.to_patches(U, geom)))
+    cs = math.sqrt(1.4)   # left state (1, 0, 1) is the fastest
+    assert math.isclose(B.cfl_dt(P_), 0.8 / (cs * 64), rel_tol=1e-14)
