@@ -114,12 +114,18 @@ def fmin(a, b):
 def fast_speed(rho, P, bn, bt1, bt2, gamma):
     """Fast magnetosonic speed along the normal whose field component is bn.
 
-    c_f^2 = 1/2 [ (gamma P + B^2)/rho + sqrt( ((gamma P + B^2)/rho)^2 - 4 gamma P bn^2 / rho^2 ) ]
+    c_f^2 = 1/2 [ (cs^2 + ca^2) + sqrt( (cs^2 + ca^2)^2 - 4 cs^2 can^2 ) ]
+    with cs^2 = gamma P / rho, ca^2 = B^2 / rho, can^2 = bn^2 / rho.  The discriminant is
+    evaluated in the algebraically identical expanded form
+    (cs^2 - can^2)^2 + cat^2 (2 (cs^2 + can^2) + cat^2), cat^2 = (bt1^2 + bt2^2) / rho,
+    whose terms are all non-negative (no cancellation when cs ~ can and B is along n).
     """
-    b2 = bn * bn + bt1 * bt1 + bt2 * bt2
-    a = (gamma * P + b2) / rho
-    disc = a * a - 4.0 * gamma * P * bn * bn / (rho * rho)
-    return torch.sqrt(0.5 * (a + safe_sqrt(disc)))
+    cs2 = gamma * P / rho
+    can2 = bn * bn / rho
+    cat2 = (bt1 * bt1 + bt2 * bt2) / rho
+    d = cs2 - can2
+    disc = d * d + cat2 * (2.0 * (cs2 + can2) + cat2)
+    return torch.sqrt(0.5 * (cs2 + can2 + cat2 + safe_sqrt(disc)))
 
 
 # ----------------------------------------------------------------------------------------

@@ -171,6 +171,18 @@ def test_zero_field_reduces_to_hllc():
         assert np.allclose(F[k], Fc[k], rtol=1e-11, atol=1e-12)
 
 
+def test_fast_speed_equals_textbook_form():
+    """The expanded discriminant equals a^2 - 4 gamma P bn^2 / rho^2 away from degeneracy."""
+    rng = np.random.default_rng(10)
+    n = 1000
+    rho, P = rng.uniform(0.2, 3, n), rng.uniform(0.1, 3, n)
+    bn, b1, b2 = rng.normal(0, 1, (3, n))
+    a = (G * P + bn ** 2 + b1 ** 2 + b2 ** 2) / rho
+    ref = np.sqrt(0.5 * (a + np.sqrt(a * a - 4 * G * P * bn ** 2 / rho ** 2)))
+    got = mhd.fast_speed(T(rho), T(P), T(bn), T(b1), T(b2), G).numpy()
+    assert np.allclose(got, ref, rtol=1e-13)
+
+
 def test_fast_speed_closed_forms():
     rho, P = T([1.3]), T([0.7])
     cs2 = G * 0.7 / 1.3
