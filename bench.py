@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the MHD bunch update on GB300.
+
+Workload (the 3D headline configuration): a 512^3 periodic MHD turbulence-like box as
+4096 patches of 32^3 cells (guard 3), rho = 1, p = 1, gamma = 5/3, B = (0.1, 0, 0),
+seeded solenoidal velocity with E(k) ~ k^-2 over 1 <= |k| <= 8 and rms Mach 1, FP32.
+One step = guard fill + CFL dt on the device + fused update (persistent kernel), the
+sequence captured in a CUDA graph.  Metric: 3D MHD cell-updates per second.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent replica of
+the box on its own GPU (the box is not split across GPUs: replicas only), and value is
+the total over ranks.  --impl reference times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D MHD cell-updates/s per GB300"
+UNIT = "cell-updates/s"
+# Algorithmic arithmetic of one cell-update: add/sub + mul + div + sqrt counted once per
+# output element of the scheme's stages (python -m oracle.flops, 32^3 patch): 1395 add,
+# 1464 mul, 282 div, 114 sqrt (plus 327 compares/selects, not counted as flops).
+FLOPS_PER_CELL = 3255.0
+BYTES_PER_CELL = {4: 64.0, 8: 128.0}       # read 8 values + write 8 values per cell-update
+SMS, FP32_LANES = 152, 128                 # GB300: SMs, FP32 lanes per SM
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks / throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f if l.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(ncell=512, patch=32):
+    from paper_2508_09568_gb300 import workloads as W
+    geom, fields, meta = W.turbulence_box(ncell=ncell, patch=patch)
+    return geom, fields, meta
+
+
+def cpu_baseline(steps=1):
+    """The oracle as it stands on host cores: 8 patches of 32^3 (a 64^3 box of the same generator)."""
+    from oracle import mhd as O
+    from paper_2508_09568_gb300 import workloads as W
+    geom, fields, meta = W.turbulence_box(ncell=64, patch=32)
+    flat = W.to_patches(fields, geom)
+    ob = O.Bunch(geom, meta["gamma"])
+    P = ob.split(flat)
+    dt = ob.cfl_dt(ob.fill_guards(P))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        P = ob.step(P, dt)
+    el = time.perf_counter() - t0
+    cells = geom.interior_cells() * steps
+    return {"value": cells / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{steps} step(s) of 8 patches of 32^3 (64^3 periodic box, same generator), FP64, "
+                      f"guard fill + step, {el:.2f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    for _ in range(warm):
+        cpu_baseline(1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        vals.append(cpu_baseline(1)["value"])
+    el = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    cb = cpu_baseline(1)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": warm, "ms_per_step": 1e3 * el / max(steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D MHD turbulence box sample: 8 patches of 32^3 per step (FP64 oracle on host)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    from paper_2508_09568_gb300 import capi
+    from paper_2508_09568_gb300 import workloads as W
+    from paper_2508_09568_gb300.bunch import MHDBunch
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    t_gen = time.perf_counter()
+    geom, fields, meta = workload(args.ncell, args.patch)
+    dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    rb = 4 if dtype == torch.float32 else 8
+    host = torch.empty(geom.state_elems(), dtype=dtype).pin_memory()
+    W.to_patches(fields, geom, dtype=np.float32 if rb == 4 else np.float64, out=host.numpy())
+    del fields
+    t_gen = time.perf_counter() - t_gen
+    cells = geom.interior_cells()
+
+    b = MHDBunch(geom, dtype=dtype, gamma=meta["gamma"], courant=0.8, device=str(dev))
+    with torch.cuda.stream(b.stream):
+        b.current().copy_(host, non_blocking=True)
+    b.stream.synchronize()
+    b.set_mode(capi.MHD_MODE_PERSISTENT, -1)
+    cfg = b.autotune(None)
+    tile = b.config_info(cfg)
+
+    # ---- timed region: graph replay of (fill -> CFL dt -> step), K steps
+    dts = torch.zeros(1, dtype=torch.float64, device=dev)
+    b.graph_capture(1, dts)
+    for _ in range(args.warmup):
+        b.graph_launch()
+    b.stream.synchronize()
+    l0 = b.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(b.stream)
+        for _ in range(args.steps):
+            b.graph_launch()
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = b.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    ms_max = allmax(ms, ws)
+    value = cells * args.steps * ws / (ms_max * 1e-3)
+    clocks = clk.summary()
+
+    # ---- per-kernel times (eager, events on the bunch stream), same state and sequence
+    dt_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(b.stream)
+        b.fill_guards()
+        ev[k][1].record(b.stream)
+        b.cfl_dt_device(dt_dev)
+        ev[k][2].record(b.stream)
+        b.step_device_dt(dt_dev)
+        ev[k][3].record(b.stream)
+    b.stream.synchronize()
+    t_fill = np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])
+    t_cfl = np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
+    t_step = np.mean([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
+    code, msg = b.error()
+    if code != 0:
+        raise RuntimeError(f"device error during the benchmark: {msg}")
+
+    # ---- the plain path: one launch per patch (same kernel), eager
+    kp = max(2, min(args.steps, 4))
+    b.set_mode(capi.MHD_MODE_PER_PATCH, cfg)
+    b.fill_guards()
+    b.cfl_dt_device(dt_dev)
+    b.step_device_dt(dt_dev)
+    b.stream.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(b.stream)
+    for _ in range(kp):
+        b.fill_guards()
+        b.cfl_dt_device(dt_dev)
+        b.step_device_dt(dt_dev)
+    p1.record(b.stream)
+    b.stream.synchronize()
+    plain = cells * kp / (p0.elapsed_time(p1) * 1e-3)
+    b.set_mode(capi.MHD_MODE_PERSISTENT, cfg)
+
+    # ---- end to end through the C ABI on host buffers (H2D + fill + dt + step + D2H per step)
+    ke = max(1, min(args.steps, 3))
+    b.advance_host(host, 1)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        b.advance_host(host, 1)
+    te = time.perf_counter() - t0
+    te = allmax(te, ws)
+    e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": b.nbytes,
+           "d2h_bytes_per_step": b.nbytes}
+
+    # ---- roofline of the dominant kernel (the fused step)
+    step_s = t_step * 1e-3
+    alu_peak = SMS * FP32_LANES * 2 * sm_max_mhz * 1e6 / 1e12 if rb == 4 else None
+    flops = FLOPS_PER_CELL * cells / step_s / 1e12
+    hbm = BYTES_PER_CELL[rb] * cells / step_s / 1e9
+    roof = {"bound": "alu", "achieved": flops, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": (flops / alu_peak) if alu_peak else None, "traffic": None,
+            "kernel": "step_kernel", "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
+            "flops_per_cell": FLOPS_PER_CELL}
+    hbm_roof = {"bound": "hbm", "achieved": hbm, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm / hbm_gbs,
+                "bytes_per_cell": BYTES_PER_CELL[rb], "peak_source": peak_src,
+                "frac_of_whole_step": (BYTES_PER_CELL[rb] * value / ws / 1e9) / hbm_gbs}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+           "config": {"workload": f"3D periodic MHD turbulence box {args.ncell}^3 as {geom.npatch} patches of "
+                                  f"{args.patch}^3 (guard 3), seeded solenoidal v, rms Mach 1, {args.dtype}; "
+                                  "step = fill + CFL dt + persistent fused update in a CUDA graph",
+                      "cells": cells, "patches": geom.npatch, "patch": args.patch,
+                      "tile": {"x": tile[0], "y": tile[1], "threads": tile[2]},
+                      "l2": f"inputs larger than L2 (state {b.nbytes / 1e9:.2f} GB per buffer)",
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "roofline": roof, "hbm_roofline": hbm_roof,
+           "kernels_ms": {"fill_guards": t_fill, "cfl_dt": t_cfl, "step": t_step},
+           "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2},
+           "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+           "setup_s": {"generate": t_gen}}
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(8)
+    b.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--ncell", type=int, default=512)
+    ap.add_argument("--patch", type=int, default=32)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * mhd_bunch.h -- C ABI of libmhdbunch.so, the GB300 (sm_103a) MHD bunch update.
+ *
+ * A *bunch* is a set of patches (small blocks of cells with ghost layers) that are
+ * advanced together, one synchronous time step at a time, by the ideal-MHD scheme of
+ * Haahr et al. (Sec. 2.1: conservative form Eqs. 1-6, adiabatic EOS; MUSCL-Hancock
+ * predictor of Sec. 2.1.4; HLLD face flux of Sec. 2.1.2; constrained transport with an
+ * edge EMF from a two-dimensional Riemann solve, Sec. 2.1.3 and Eq. 12).  Patch
+ * bunching is Secs. 2.3-2.4 of the paper.
+ *
+ * State layout (shared by every entry point): the state is ONE device buffer of reals
+ * (float when real_bytes == 4, double when 8).  Patch p starts at element
+ * patch_offsets[p] (from mhd_bunch_state_size) and is stored as [8][Z][Y][X], x fastest,
+ * variables (rho, rho*u, rho*v, rho*w, E, Bx, By, Bz).  Active axes carry `guard` ghost
+ * cells on each side; an axis whose box extent is 1 is collapsed and carries none.
+ * Bx at local x-index i is the face field on the low x-face of cell i (the index
+ * convention of Eqs. 8-12); By, Bz likewise on the low y- and z-faces.
+ *
+ * Ownership: the caller owns the two state buffers and the CUDA stream (they are only
+ * borrowed through mhd_bunch_bind).  The library owns the device patch table, its work
+ * buffers, the CUDA graph and the error word, all released by mhd_bunch_destroy.
+ *
+ * Errors: every function returns an mhd_status (0 on success) and never aborts or throws
+ * across the ABI.  mhd_last_error() gives a thread-local message for the last failure.
+ * Problems found on the device (non-finite or non-positive density / energy after an
+ * update, bad patch-table entries, a bounded wait that ran out) are latched in a device
+ * error word and reported by the next call that synchronises (mhd_bunch_cfl_dt,
+ * mhd_bunch_get_error, mhd_bunch_advance_host).
+ *
+ * Threading: calls on one handle are stream-ordered on the bound stream and must not be
+ * made from several host threads at once.  Different handles are independent.
+ */
+#ifndef MHD_BUNCH_H
+#define MHD_BUNCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_bunch mhd_bunch;
+
+typedef enum {
+    MHD_OK = 0,
+    MHD_EINVAL = -1,    /* invalid argument (sizes, nvar, guard, null pointer, bad table) */
+    MHD_ENOMEM = -2,    /* device or host allocation failed */
+    MHD_ECUDA = -3,     /* a CUDA runtime call failed */
+    MHD_EPHYS = -4,     /* the device found a non-physical state (rho <= 0, non-finite) */
+    MHD_EBOUNDS = -5,   /* the device found an index outside the patch table / buffers */
+    MHD_ETIMEOUT = -6,  /* a bounded device wait ran out */
+    MHD_ESTATE = -7     /* call out of order (e.g. step before bind / set_geometry) */
+} mhd_status;
+
+enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
+enum { MHD_LIMITER_MINMOD = 0, MHD_LIMITER_MC = 1 };
+
+/* How mhd_bunch_step launches the update kernel.
+ *   PER_PATCH  : one launch per patch (the plain path),
+ *   BUNCHED    : one launch over every tile of every patch,
+ *   PERSISTENT : one launch of (SM count x resident CTAs) CTAs that pull tiles from a
+ *                device work counter until the bunch is done.                          */
+enum { MHD_MODE_PER_PATCH = 0, MHD_MODE_BUNCHED = 1, MHD_MODE_PERSISTENT = 2 };
+
+/* Create a bunch of npatch equal patches of nx*ny*nz active cells.
+ * guard: ghost width on active axes; must be >= 3 (the update reads two ghost cells
+ *        plus the far face of the normal field; the paper's patches use 3, Sec. 3.2).
+ * nvar : must be 8.  real_bytes: 4 (float) or 8 (double).
+ * A dimension of 1 marks a collapsed axis; the active axes must be x, x-y or x-y-z.
+ * On success *out holds a new handle.  Returns MHD_EINVAL on bad sizes. */
+int mhd_bunch_create(int nx, int ny, int nz, int guard, int nvar, int npatch,
+                     int real_bytes, mhd_bunch **out);
+
+/* As mhd_bunch_create, with per-patch sizes: patch_n is host int32[npatch*3]
+ * (nx, ny, nz per patch).  The array is copied. */
+int mhd_bunch_create_ragged(const int32_t *patch_n, int npatch, int guard, int nvar,
+                            int real_bytes, mhd_bunch **out);
+
+/* Place the patches in the box (needed by the guard fill, Sec. 2.2: DISPATCH fills ghost
+ * zones from neighbouring patches).
+ * dx           host double[3]: cell size along x, y, z.
+ * patch_origin host int64[npatch*3]: global cell index of each patch's first active cell.
+ * domain_cells host int64[3]: cells of the whole box; extent 1 on collapsed axes.
+ * bc           host int32[6]: (x_lo, x_hi, y_lo, y_hi, z_lo, z_hi) boundary kinds,
+ *              MHD_BC_PERIODIC or MHD_BC_OUTFLOW (zero-gradient copy).
+ * The patches must tile the box exactly (checked; MHD_EINVAL otherwise). */
+int mhd_bunch_set_geometry(mhd_bunch *b, const double dx[3], const int64_t *patch_origin,
+                           const int64_t domain_cells[3], const int32_t bc[6]);
+
+/* Scheme parameters: adiabatic index, Courant number for mhd_bunch_cfl_dt, slope limiter
+ * (MHD_LIMITER_MINMOD or MHD_LIMITER_MC).  Defaults: 5/3, 0.8, minmod. */
+int mhd_bunch_set_params(mhd_bunch *b, double gamma, double courant, int limiter);
+
+/* Bytes of one state buffer; if patch_offsets is not NULL it receives npatch int64 element
+ * offsets (in reals) of the patches inside the buffer. */
+int mhd_bunch_state_size(const mhd_bunch *b, size_t *bytes, int64_t *patch_offsets);
+
+/* Borrow the caller's device buffers (state = current U^n, state_next = where U^{n+1}
+ * is written) and CUDA stream (a cudaStream_t, NULL for the legacy default stream).
+ * Both buffers must hold mhd_bunch_state_size bytes and be 16-byte aligned. */
+int mhd_bunch_bind(mhd_bunch *b, void *state, void *state_next, void *cuda_stream);
+
+/* Device pointer of the buffer that currently holds U^n (the two bound buffers swap
+ * roles after every step). */
+int mhd_bunch_current(const mhd_bunch *b, void **state);
+
+/* a1: fill every ghost cell of every patch with the box cell it stands for (a copy from
+ * the owning patch at the same time, periodic wrap or zero-gradient at the box ends).
+ * Stream-ordered, asynchronous. */
+int mhd_bunch_fill_guards(mhd_bunch *b);
+
+/* a2: CFL time step dt = courant / max_cells sum_d (|u_d| + c_f,d)/dx_d over the
+ * interior cells of all patches (synchronous bunch time step).  Reads the ghost faces
+ * next to the interior, so call after mhd_bunch_fill_guards.
+ * _device writes the double into dt_dev (device memory) without synchronising;
+ * the host variant synchronises the stream and checks the device error word. */
+int mhd_bunch_cfl_dt(mhd_bunch *b, double *dt_host);
+int mhd_bunch_cfl_dt_device(mhd_bunch *b, void *dt_dev);
+
+/* a3-a9: advance every patch by dt: reads U^n (ghosts filled) from the current buffer,
+ * writes the interior cells and owned faces of U^{n+1} into the other one, then swaps
+ * the two.  Ghost cells of the new state are stale until the next fill. */
+int mhd_bunch_step(mhd_bunch *b, double dt);
+/* As mhd_bunch_step with dt read on the device from dt_dev (double). */
+int mhd_bunch_step_device_dt(mhd_bunch *b, const void *dt_dev);
+
+/* Launch mode of the update (MHD_MODE_*) and tile configuration index (0..n-1 from
+ * mhd_bunch_num_configs; -1 = library default).  Every mode and every configuration
+ * computes bitwise the same state. */
+int mhd_bunch_set_mode(mhd_bunch *b, int mode, int config);
+int mhd_bunch_num_configs(const mhd_bunch *b, int *nconfig);
+int mhd_bunch_config_info(const mhd_bunch *b, int config, int *tile_x, int *tile_y,
+                          int *threads);
+
+/* Time each tile configuration on the bound state (a few steps each, the state is
+ * restored afterwards) and keep the fastest.  If cache_path is not NULL the choice is
+ * read from / written to that text file, keyed by device, precision and patch sizes. */
+int mhd_bunch_autotune(mhd_bunch *b, const char *cache_path, int *chosen);
+
+/* Capture nsteps of (fill guards -> CFL dt on the device -> step with the device dt) into
+ * a CUDA graph on the bound stream (which must not be the legacy default stream);
+ * mhd_bunch_graph_launch replays it and swaps the buffers as the eager steps would.
+ * dt_dev (device double[nsteps], may be NULL) receives the dt of each replayed step.
+ * Any later set_geometry / set_params / set_mode / bind discards the graph. */
+int mhd_bunch_graph_capture(mhd_bunch *b, int nsteps, void *dt_dev);
+int mhd_bunch_graph_launch(mhd_bunch *b);
+
+/* End-to-end helper working on HOST memory: copies host_state (state_size bytes, layout
+ * above) to the current device buffer, runs nsteps of fill -> CFL dt -> step, copies the
+ * final state back into host_state and returns the simulated time advanced in *t_out.
+ * Synchronises the bound stream. */
+int mhd_bunch_advance_host(mhd_bunch *b, void *host_state, int nsteps, double *t_out);
+
+/* Adjoint of one step at fixed dt (the reverse of mhd_bunch_step, including the guard
+ * fill): given U^n (interior valid; ghosts are re-filled internally) and the cotangent
+ * lam_next of U^{n+1} (interior cells and owned faces), writes
+ * lam = (dU^{n+1}/dU^n)^T lam_next on the interior cells and owned faces, summing the
+ * contributions that reached ghost copies back into the cells they copy.  All three are
+ * device buffers in the state layout; lam is overwritten.  Ghost entries of lam_next are
+ * ignored and those of lam are set to 0.  Non-differentiable points take the subgradient
+ * of the forward branch (limiter: the selected argument, zero when the arguments differ
+ * in sign; wave-speed max/min: the selected argument, first on ties). */
+int mhd_bunch_step_adjoint(mhd_bunch *b, double dt, const void *U_n, const void *lam_next,
+                           void *lam);
+
+/* Device error word: *code receives the latched mhd_status (MHD_OK if none) and msg (if
+ * not NULL) a description; the word is cleared.  Synchronises the stream. */
+int mhd_bunch_get_error(mhd_bunch *b, int *code, char *msg, size_t len);
+
+/* Number of the library's own kernel launches issued on this handle so far. */
+int mhd_bunch_launch_count(const mhd_bunch *b, int64_t *count);
+
+void mhd_bunch_destroy(mhd_bunch *b);
+
+/* Thread-local text of the last error returned by any call on this thread. */
+const char *mhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHD_BUNCH_H */

@@ -1,0 +1,166 @@
+"""Python handle of a device-resident MHD bunch (thin wrapper over the C ABI).
+
+PyTorch provides the device memory (two state buffers) and the CUDA stream; every
+operation is one or more calls into libmhdbunch.so.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+import torch
+
+from . import capi
+from .workloads import Geometry
+
+
+class MHDBunch:
+    """A bunch of patches on one GPU.
+
+    geom     workloads.Geometry (patch sizes, origins, box, dx, boundary kinds, guard)
+    dtype    torch.float32 or torch.float64 (arithmetic precision of the kernels)
+    """
+
+    def __init__(self, geom: Geometry, dtype=torch.float32, gamma=5.0 / 3.0, courant=0.8, limiter=0,
+                 device="cuda:0", stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("MHDBunch needs a CUDA device (no CPU fallback)")
+        self.lib = capi.load()
+        self.geom = geom
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.rb = 4 if dtype == torch.float32 else 8
+        torch.cuda.set_device(self.device)
+        # a dedicated stream by default: the legacy default stream cannot be captured in a graph
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = ct.c_void_p()
+        pn = np.ascontiguousarray(geom.patch_n.astype(np.int32))
+        capi.check(self.lib.mhd_bunch_create_ragged(pn.ctypes.data_as(capi.I32P), geom.npatch, int(geom.guard), 8,
+                                                    self.rb, ct.byref(h)))
+        self.h = h
+        try:
+            dx = np.ascontiguousarray(geom.dx, dtype=np.float64)
+            org = np.ascontiguousarray(geom.origin, dtype=np.int64)
+            dom = np.ascontiguousarray(geom.domain, dtype=np.int64)
+            bc = np.ascontiguousarray(geom.bc.reshape(-1), dtype=np.int32)
+            capi.check(self.lib.mhd_bunch_set_geometry(h, dx.ctypes.data_as(capi.DP), org.ctypes.data_as(capi.I64P),
+                                                       dom.ctypes.data_as(capi.I64P), bc.ctypes.data_as(capi.I32P)))
+            capi.check(self.lib.mhd_bunch_set_params(h, float(gamma), float(courant), int(limiter)))
+            nbytes = ct.c_size_t()
+            offs = np.zeros(geom.npatch, dtype=np.int64)
+            capi.check(self.lib.mhd_bunch_state_size(h, ct.byref(nbytes), offs.ctypes.data_as(capi.I64P)))
+            if not np.array_equal(offs, geom.offsets()):
+                raise RuntimeError("library state layout differs from the workload layout")
+            self.nbytes = nbytes.value
+            n = self.nbytes // self.rb
+            with torch.cuda.stream(self.stream):
+                self.buf = [torch.full((n,), float("nan"), dtype=dtype, device=self.device) for _ in range(2)]
+            capi.check(self.lib.mhd_bunch_bind(h, ct.c_void_p(self.buf[0].data_ptr()),
+                                               ct.c_void_p(self.buf[1].data_ptr()),
+                                               ct.c_void_p(self.stream.cuda_stream)))
+        except Exception:
+            self.lib.mhd_bunch_destroy(h)
+            self.h = None
+            raise
+
+    # -- state ------------------------------------------------------------------------
+    def current(self) -> torch.Tensor:
+        p = ct.c_void_p()
+        capi.check(self.lib.mhd_bunch_current(self.h, ct.byref(p)))
+        for t in self.buf:
+            if t.data_ptr() == p.value:
+                return t
+        raise RuntimeError("current buffer not found")
+
+    def upload(self, flat: np.ndarray):
+        cur = self.current()
+        src = torch.from_numpy(np.ascontiguousarray(flat).astype(np.float64 if self.rb == 8 else np.float32))
+        with torch.cuda.stream(self.stream):
+            cur.copy_(src.to(self.device, non_blocking=False))
+
+    def download(self) -> np.ndarray:
+        self.stream.synchronize()
+        return self.current().cpu().numpy()
+
+    # -- the path -------------------------------------------------------------------------
+    def fill_guards(self):
+        capi.check(self.lib.mhd_bunch_fill_guards(self.h))
+
+    def cfl_dt(self) -> float:
+        dt = ct.c_double()
+        capi.check(self.lib.mhd_bunch_cfl_dt(self.h, ct.byref(dt)))
+        return dt.value
+
+    def cfl_dt_device(self, dt_dev: torch.Tensor):
+        assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
+        capi.check(self.lib.mhd_bunch_cfl_dt_device(self.h, ct.c_void_p(dt_dev.data_ptr())))
+
+    def step(self, dt: float):
+        capi.check(self.lib.mhd_bunch_step(self.h, float(dt)))
+
+    def step_device_dt(self, dt_dev: torch.Tensor):
+        assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
+        capi.check(self.lib.mhd_bunch_step_device_dt(self.h, ct.c_void_p(dt_dev.data_ptr())))
+
+    def set_mode(self, mode: int, config: int = -1):
+        capi.check(self.lib.mhd_bunch_set_mode(self.h, int(mode), int(config)))
+
+    def num_configs(self) -> int:
+        n = ct.c_int()
+        capi.check(self.lib.mhd_bunch_num_configs(self.h, ct.byref(n)))
+        return n.value
+
+    def config_info(self, k: int):
+        tx, ty, nt = ct.c_int(), ct.c_int(), ct.c_int()
+        capi.check(self.lib.mhd_bunch_config_info(self.h, k, ct.byref(tx), ct.byref(ty), ct.byref(nt)))
+        return tx.value, ty.value, nt.value
+
+    def autotune(self, cache_path: str | None = None) -> int:
+        c = ct.c_int()
+        capi.check(self.lib.mhd_bunch_autotune(self.h, cache_path.encode() if cache_path else None, ct.byref(c)))
+        return c.value
+
+    def graph_capture(self, nsteps: int, dt_dev: torch.Tensor | None = None):
+        ptr = ct.c_void_p(dt_dev.data_ptr()) if dt_dev is not None else None
+        capi.check(self.lib.mhd_bunch_graph_capture(self.h, int(nsteps), ptr))
+
+    def graph_launch(self):
+        capi.check(self.lib.mhd_bunch_graph_launch(self.h))
+
+    def advance_host(self, host_state: torch.Tensor, nsteps: int) -> float:
+        """End to end on host memory (pinned torch tensor in the state layout), in place."""
+        assert host_state.device.type == "cpu" and host_state.dtype == self.dtype
+        assert host_state.numel() * self.rb == self.nbytes
+        t = ct.c_double()
+        capi.check(self.lib.mhd_bunch_advance_host(self.h, ct.c_void_p(host_state.data_ptr()), int(nsteps),
+                                                   ct.byref(t)))
+        return t.value
+
+    def step_adjoint(self, dt: float, U_n: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor):
+        for t in (U_n, lam_next, lam):
+            assert t.is_cuda and t.dtype == self.dtype and t.numel() * self.rb == self.nbytes
+        capi.check(self.lib.mhd_bunch_step_adjoint(self.h, float(dt), ct.c_void_p(U_n.data_ptr()),
+                                                   ct.c_void_p(lam_next.data_ptr()), ct.c_void_p(lam.data_ptr())))
+
+    def error(self):
+        code = ct.c_int()
+        msg = ct.create_string_buffer(256)
+        capi.check(self.lib.mhd_bunch_get_error(self.h, ct.byref(code), msg, 256))
+        return code.value, msg.value.decode()
+
+    def launch_count(self) -> int:
+        n = ct.c_int64()
+        capi.check(self.lib.mhd_bunch_launch_count(self.h, ct.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.stream.synchronize()
+            self.lib.mhd_bunch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,82 @@
+// Instantiation helpers shared by the per-precision translation units.
+#pragma once
+
+#include "mhd_aux.cuh"
+#include "mhd_launch.h"
+#include "mhd_step.cuh"
+
+namespace mhd {
+
+template <typename R>
+static StepArgs<R> to_args(const StepHostArgs& h) {
+    StepArgs<R> a;
+    a.U = static_cast<const R*>(h.U);
+    a.Unew = static_cast<R*>(h.Unew);
+    a.patches = h.patches;
+    a.tiles = h.tiles;
+    a.ntiles = h.ntiles;
+    a.dynamic = h.dynamic;
+    a.work = h.work;
+    a.dt_ptr = h.dt_ptr;
+    a.dt_val = h.dt_val;
+    a.gamma = h.gamma;
+    a.eps = h.eps;
+    for (int d = 0; d < 3; ++d) a.dxi[d] = h.dxi[d];
+    a.limiter = h.limiter;
+    a.err = h.err;
+    return a;
+}
+
+template <typename R, int NDIM, int TX, int TY, int NT>
+struct StepInst {
+    using C = StepCfg<R, NDIM, TX, TY, NT>;
+    static_assert(C::SMEM_BYTES <= 227 * 1024, "tile too large for shared memory");
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+    }
+    static cudaError_t occupancy(int* blocks) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_kernel<R, NDIM, TX, TY, NT>, NT,
+                                                             C::SMEM_BYTES);
+    }
+    static cudaError_t launch(const void* args, int grid, cudaStream_t s) {
+        const StepArgs<R> a = to_args<R>(*static_cast<const StepHostArgs*>(args));
+        step_kernel<R, NDIM, TX, TY, NT><<<grid, NT, C::SMEM_BYTES, s>>>(a);
+        return cudaGetLastError();
+    }
+    static StepLaunch entry() {
+        return StepLaunch{NDIM, C::TX, C::TY, NT, C::SMEM_BYTES, &prepare, &occupancy, &launch};
+    }
+};
+
+template <typename R>
+static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, const FillGeom& fg, unsigned* err,
+                               cudaStream_t s) {
+    dim3 grid(8, npatch < 65535 ? npatch : 65535);
+    fill_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U), patches, npatch, fg, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_cfl(const void* U, const PatchDev* patches, int npatch, double gamma, double courant,
+                              const double dxi[3], const int act[3], void* partial, int grid, unsigned* counter,
+                              double* dt_out, unsigned* err, cudaStream_t s) {
+    CflArgs<R> a;
+    a.U = static_cast<const R*>(U);
+    a.patches = patches;
+    a.npatch = npatch;
+    a.gamma = gamma;
+    a.courant = courant;
+    for (int d = 0; d < 3; ++d) {
+        a.dxi[d] = dxi[d];
+        a.act[d] = act[d];
+    }
+    a.partial = static_cast<R*>(partial);
+    a.counter = counter;
+    a.dt_out = dt_out;
+    a.err = err;
+    cfl_kernel<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mhd

@@ -1,0 +1,185 @@
+// Guard fill (a1) and CFL time step (a2) kernels.
+#pragma once
+
+#include "mhd_common.cuh"
+#include "mhd_math.cuh"
+
+namespace mhd {
+
+// ---------------------------------------------------------------------------------------
+// a1: guard fill.  Every ghost cell of every patch receives the value (all 8 variables)
+// of the box cell it stands for: its global index is wrapped (periodic) or clamped
+// (zero-gradient outflow) into the box, the owning patch is read from the owner map and
+// the value is copied from that patch's interior.  Sources are always interior cells and
+// destinations always ghost cells, so the kernel is race free.  DISPATCH fills ghost
+// zones from neighbouring patches (Sec. 2.2, Sec. 3.1); here all patches share one time.
+// ---------------------------------------------------------------------------------------
+
+// number of ghost cells of a padded patch
+__device__ __forceinline__ int ghost_count(const PatchDev& p) {
+    return p.X * p.Y * p.Z - p.nx * p.ny * p.nz;
+}
+
+// k-th ghost cell of a patch -> local padded coordinates (slabs: z, then y, then x)
+__device__ __forceinline__ void ghost_coord(const PatchDev& p, int k, int& x, int& y, int& z) {
+    const int cz = 2 * p.gz * p.X * p.Y;
+    const int cy = 2 * p.gy * p.X * p.nz;
+    if (k < cz) {
+        const int per = p.gz * p.X * p.Y;
+        const int side = k / per, r = k - side * per;
+        z = (side ? p.gz + p.nz : 0) + r / (p.X * p.Y);
+        const int r2 = r % (p.X * p.Y);
+        y = r2 / p.X;
+        x = r2 % p.X;
+        return;
+    }
+    k -= cz;
+    if (k < cy) {
+        const int per = p.gy * p.X * p.nz;
+        const int side = k / per, r = k - side * per;
+        z = p.gz + r / (p.gy * p.X);
+        const int r2 = r % (p.gy * p.X);
+        y = (side ? p.gy + p.ny : 0) + r2 / p.X;
+        x = r2 % p.X;
+        return;
+    }
+    k -= cy;
+    const int per = p.gx * p.ny * p.nz;
+    const int side = k / per, r = k - side * per;
+    z = p.gz + r / (p.gx * p.ny);
+    const int r2 = r % (p.gx * p.ny);
+    y = p.gy + r2 / p.gx;
+    x = (side ? p.gx + p.nx : 0) + r2 % p.gx;
+}
+
+__device__ __forceinline__ int wrap_axis(int g, int N, int lo, int hi) {
+    if (g < 0) return lo == 0 ? ((g % N) + N) % N : 0;
+    if (g >= N) return hi == 0 ? g % N : N - 1;
+    return g;
+}
+
+template <typename R>
+__global__ void fill_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches, int npatch,
+                            FillGeom fg, unsigned* err) {
+    for (int p = blockIdx.y; p < npatch; p += gridDim.y) {
+        const PatchDev pt = patches[p];
+        const int ng = ghost_count(pt);
+        const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
+            int x, y, z;
+            ghost_coord(pt, k, x, y, z);
+            const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
+            const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
+            const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
+            const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
+            if (ow < 0 || ow >= npatch) {
+                atomicOr(err, ERR_BOUNDS);
+                continue;
+            }
+            const PatchDev src = patches[ow];
+            const int sx = gxg - src.ox + src.gx, sy = gyg - src.oy + src.gy, sz = gzg - src.oz + src.gz;
+            const int64_t svol = (int64_t)src.X * src.Y * src.Z;
+            const R* s = U + src.off + ((int64_t)sz * src.Y + sy) * src.X + sx;
+            R* d = U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) d[v * vol] = s[v * svol];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a2: CFL time step.  rate = sum over active axes of (|u_d| + c_f,d) / dx_d per interior
+// cell; each block reduces its patches' maximum (warp shuffles, then shared memory) into
+// partial[block]; the last block to finish reduces the partials and writes
+// dt = courant / max_rate into *dt_out (double).  Non-finite rates set ERR_PHYS.
+// ---------------------------------------------------------------------------------------
+
+template <typename R>
+__device__ __forceinline__ R block_max(R v, R* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : R(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            R w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+    }
+    return v;   // valid in thread 0
+}
+
+template <typename R>
+struct CflArgs {
+    const R* __restrict__ U;
+    const PatchDev* __restrict__ patches;
+    int npatch;
+    double gamma, courant;
+    double dxi[3];
+    int act[3];
+    R* partial;            // [gridDim.x] scratch
+    unsigned* counter;     // scratch, zero before the launch, left at zero after
+    double* dt_out;
+    unsigned* err;
+};
+
+template <typename R>
+__global__ void cfl_kernel(CflArgs<R> a) {
+    __shared__ R red[32];
+    __shared__ bool last;
+    const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0);
+    const R dxi0 = R(a.dxi[0]), dxi1 = R(a.dxi[1]), dxi2 = R(a.dxi[2]);
+    R vmax = R(0);
+    bool bad = false;
+    for (int p = blockIdx.x; p < a.npatch; p += gridDim.x) {
+        const PatchDev pt = a.patches[p];
+        const int n = pt.nx * pt.ny * pt.nz;
+        const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
+        const int sy = pt.X, sz = pt.X * pt.Y;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
+            const R* c = a.U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+            const R bxc = R(0.5) * (c[5 * vol] + c[5 * vol + 1]);
+            const R byc = a.act[1] ? R(0.5) * (c[6 * vol] + c[6 * vol + sy]) : c[6 * vol];
+            const R bzc = a.act[2] ? R(0.5) * (c[7 * vol] + c[7 * vol + sz]) : c[7 * vol];
+            R q[8];
+            cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
+            const R ri = R(1) / q[Q_RHO], gP = gamma * q[Q_P];
+            R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
+            if (a.act[1]) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
+            if (a.act[2]) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;
+            if (!isfinite((double)rate)) bad = true;
+            else vmax = rate > vmax ? rate : vmax;
+        }
+    }
+    if (bad) atomicOr(a.err, ERR_PHYS);
+    R bm = block_max(vmax, red);
+    if (threadIdx.x == 0) {
+        a.partial[blockIdx.x] = bm;
+        __threadfence();
+        last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        R v = R(0);
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+            R w = ((volatile R*)a.partial)[k];
+            v = w > v ? w : v;
+        }
+        __syncthreads();
+        v = block_max(v, red);
+        if (threadIdx.x == 0) {
+            *a.dt_out = a.courant / (double)v;
+            *a.counter = 0u;
+        }
+    }
+}
+
+}  // namespace mhd

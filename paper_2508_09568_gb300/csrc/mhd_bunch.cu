@@ -1,0 +1,762 @@
+// Host runtime and C ABI of libmhdbunch.so (declared in include/mhd_bunch.h).
+//
+// Owns the device patch table, the owner map used by the guard fill, the tile lists of
+// every compiled kernel configuration, the small work buffers (CFL partial maxima, work
+// counters, error word) and the CUDA graph.  The state buffers and the stream belong to
+// the caller.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd_bunch.h"
+#include "mhd_launch.h"
+
+using namespace mhd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(MHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// degenerate-star threshold of the HLLD solver, relative to Bn^2, per precision
+double hlld_eps(int rb) { return rb == 8 ? 1e-12 : 1e-6; }
+
+}  // namespace
+
+struct mhd_bunch {
+    int rb = 4, guard = 3, npatch = 0, ndim = 3;
+    std::vector<int> pn;                 // 3 * npatch
+    bool have_geom = false;
+    double dx[3] = {1, 1, 1};
+    std::vector<int64_t> origin;
+    int64_t domain[3] = {1, 1, 1};
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    double gamma = 5.0 / 3.0, courant = 0.8;
+    int limiter = 0;
+    std::vector<int64_t> offs;
+    size_t state_bytes = 0;
+    std::vector<PatchDev> hp;
+    PatchDev* d_patches = nullptr;
+    int* d_owner = nullptr;
+    FillGeom fg{};
+    // tiles of each step configuration: natural (per patch) order and cost-sorted order
+    struct Tiles {
+        int4* d_nat = nullptr;
+        int4* d_lpt = nullptr;
+        int n = 0;
+        std::vector<int> first, count;   // per patch, in natural order
+    };
+    std::vector<Tiles> tiles;
+    std::vector<int> cfg_index;          // compiled configs usable for this ndim
+    int* d_work = nullptr;               // 2 ints (persistent work counter, finished CTAs)
+    void* d_partial = nullptr;           // CFL partial maxima
+    unsigned* d_counter = nullptr;       // CFL last-block counter
+    int cfl_grid = 0;
+    double* d_dt = nullptr;              // dt of the host-dt entry points
+    double* d_dts = nullptr;             // dt per step of advance_host
+    int d_dts_cap = 0;
+    unsigned* d_err = nullptr;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;                         // index of the buffer holding U^n
+    cudaStream_t stream = nullptr;
+    int mode = MHD_MODE_PERSISTENT, config = -1;
+    // captured step sequences; with an odd step count the second starts from the other buffer
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_steps = 0, graph_start = 0;
+    int64_t launches = 0;
+    int nsm = 0;
+    const PrecisionKernels* K = nullptr;
+};
+
+namespace {
+
+bool active(const mhd_bunch* b, int d) { return b->domain[d] > 1; }
+
+int default_config(const mhd_bunch* b) {
+    // first compiled configuration for this dimensionality
+    return b->cfg_index.empty() ? -1 : 0;
+}
+
+const StepLaunch& step_cfg(const mhd_bunch* b, int k) { return b->K->step[b->cfg_index[k]]; }
+
+void free_tiles(mhd_bunch* b) {
+    for (auto& t : b->tiles) {
+        cudaFree(t.d_nat);
+        cudaFree(t.d_lpt);
+    }
+    b->tiles.clear();
+}
+
+void release_graph(mhd_bunch* b) {
+    for (int k = 0; k < 2; ++k) {
+        if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
+        if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+        b->gexec[k] = nullptr;
+        b->graph[k] = nullptr;
+    }
+    b->graph_steps = 0;
+}
+
+int common_create(const int32_t* pn, int npatch, int guard, int nvar, int rb, mhd_bunch** out) {
+    if (!out) return fail(MHD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nvar != 8) return fail(MHD_EINVAL, "nvar must be 8 (rho, 3 momenta, E, 3 face fields)");
+    if (rb != 4 && rb != 8) return fail(MHD_EINVAL, "real_bytes must be 4 or 8");
+    if (guard < 3) return fail(MHD_EINVAL, "guard must be >= 3");
+    if (npatch <= 0 || !pn) return fail(MHD_EINVAL, "npatch must be positive");
+    // dimensionality from the first patch; all patches must agree on which axes are active
+    int act[3];
+    for (int d = 0; d < 3; ++d) act[d] = pn[d] > 1;
+    int ndim = act[2] ? 3 : (act[1] ? 2 : 1);
+    if ((act[2] && !act[1]) || (act[1] && !act[0]) || !act[0])
+        return fail(MHD_EINVAL, "active axes must be x, x-y or x-y-z");
+    for (int p = 0; p < npatch; ++p)
+        for (int d = 0; d < 3; ++d) {
+            if (pn[3 * p + d] < 1) return fail(MHD_EINVAL, "patch sizes must be >= 1");
+            if ((pn[3 * p + d] > 1) != (act[d] != 0))
+                return fail(MHD_EINVAL, "all patches must share the collapsed axes");
+            if (pn[3 * p + d] > 4096) return fail(MHD_EINVAL, "patch extent too large");
+        }
+    mhd_bunch* b = new (std::nothrow) mhd_bunch();
+    if (!b) return fail(MHD_ENOMEM, "host allocation failed");
+    b->rb = rb;
+    b->guard = guard;
+    b->npatch = npatch;
+    b->ndim = ndim;
+    b->pn.assign(pn, pn + 3 * npatch);
+    b->K = rb == 4 ? &kernels_f32() : &kernels_f64();
+    for (int k = 0; k < b->K->nstep; ++k)
+        if (b->K->step[k].ndim == ndim) b->cfg_index.push_back(k);
+    // layout
+    b->offs.resize(npatch);
+    int64_t off = 0;
+    b->hp.resize(npatch);
+    for (int p = 0; p < npatch; ++p) {
+        PatchDev& q = b->hp[p];
+        q.nx = pn[3 * p];
+        q.ny = pn[3 * p + 1];
+        q.nz = pn[3 * p + 2];
+        q.gx = act[0] ? guard : 0;
+        q.gy = act[1] ? guard : 0;
+        q.gz = act[2] ? guard : 0;
+        q.X = q.nx + 2 * q.gx;
+        q.Y = q.ny + 2 * q.gy;
+        q.Z = q.nz + 2 * q.gz;
+        q.off = off;
+        q.ox = q.oy = q.oz = 0;
+        q.pad = 0;
+        b->offs[p] = off;
+        off += 8LL * q.X * q.Y * q.Z;
+        // keep every patch 16-byte aligned
+        const int64_t al = 16 / rb;
+        off = (off + al - 1) / al * al;
+    }
+    b->state_bytes = (size_t)off * rb;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(MHD_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    for (int k : b->cfg_index) {
+        e = b->K->step[k].prepare();
+        if (e != cudaSuccess) {
+            delete b;
+            return fail(MHD_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+        }
+    }
+    b->cfl_grid = std::min(npatch, b->nsm * 8);
+    e = cudaMalloc(&b->d_patches, sizeof(PatchDev) * npatch);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_work, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_partial, (size_t)b->cfl_grid * rb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_dt, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_work, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        mhd_bunch_destroy(b);
+        return fail(MHD_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return MHD_OK;
+}
+
+int64_t gcd64(int64_t a, int64_t b) { return b == 0 ? a : gcd64(b, a % b); }
+
+int build_tiles(mhd_bunch* b) {
+    free_tiles(b);
+    b->tiles.resize(b->cfg_index.size());
+    for (size_t k = 0; k < b->cfg_index.size(); ++k) {
+        const StepLaunch& L = step_cfg(b, (int)k);
+        std::vector<int4> nat;
+        auto& T = b->tiles[k];
+        T.first.resize(b->npatch);
+        T.count.resize(b->npatch);
+        for (int p = 0; p < b->npatch; ++p) {
+            T.first[p] = (int)nat.size();
+            const int nx = b->pn[3 * p], ny = b->pn[3 * p + 1], nz = b->pn[3 * p + 2];
+            for (int y0 = 0; y0 < (b->ndim >= 2 ? ny : 1); y0 += (b->ndim >= 2 ? L.ty : 1))
+                for (int x0 = 0; x0 < nx; x0 += L.tx) {
+                    const int w = std::min(L.tx, nx - x0) * (b->ndim >= 2 ? std::min(L.ty, ny - y0) : 1);
+                    nat.push_back(make_int4(p, x0, y0, w * nz));
+                }
+            T.count[p] = (int)nat.size() - T.first[p];
+        }
+        std::vector<int4> lpt = nat;
+        std::stable_sort(lpt.begin(), lpt.end(), [](const int4& a, const int4& c) { return a.w > c.w; });
+        T.n = (int)nat.size();
+        CK(cudaMalloc(&T.d_nat, sizeof(int4) * T.n));
+        CK(cudaMalloc(&T.d_lpt, sizeof(int4) * T.n));
+        CK(cudaMemcpy(T.d_nat, nat.data(), sizeof(int4) * T.n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(T.d_lpt, lpt.data(), sizeof(int4) * T.n, cudaMemcpyHostToDevice));
+    }
+    return MHD_OK;
+}
+
+StepHostArgs step_args(mhd_bunch* b, const double* dt_ptr, double dt_val) {
+    StepHostArgs a;
+    a.U = b->buf[b->cur];
+    a.Unew = b->buf[1 - b->cur];
+    a.patches = b->d_patches;
+    a.tiles = nullptr;
+    a.ntiles = 0;
+    a.dynamic = 0;
+    a.work = b->d_work;
+    a.dt_ptr = dt_ptr;
+    a.dt_val = dt_val;
+    a.gamma = b->gamma;
+    a.eps = hlld_eps(b->rb);
+    for (int d = 0; d < 3; ++d) a.dxi[d] = 1.0 / b->dx[d];
+    a.limiter = b->limiter;
+    a.err = b->d_err;
+    return a;
+}
+
+int ready(const mhd_bunch* b) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (!b->have_geom) return fail(MHD_ESTATE, "mhd_bunch_set_geometry has not been called");
+    if (!b->buf[0] || !b->buf[1]) return fail(MHD_ESTATE, "mhd_bunch_bind has not been called");
+    return MHD_OK;
+}
+
+int do_fill(mhd_bunch* b) {
+    CK(b->K->fill(b->buf[b->cur], b->d_patches, b->npatch, b->fg, b->d_err, b->stream));
+    b->launches++;
+    return MHD_OK;
+}
+
+int do_cfl(mhd_bunch* b, double* dt_dev) {
+    double dxi[3];
+    int act[3];
+    for (int d = 0; d < 3; ++d) {
+        dxi[d] = 1.0 / b->dx[d];
+        act[d] = active(b, d);
+    }
+    CK(b->K->cfl(b->buf[b->cur], b->d_patches, b->npatch, b->gamma, b->courant, dxi, act, b->d_partial,
+                 b->cfl_grid, b->d_counter, dt_dev, b->d_err, b->stream));
+    b->launches++;
+    return MHD_OK;
+}
+
+int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
+    if (b->cfg_index.empty()) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
+    const int k = b->config < 0 ? default_config(b) : b->config;
+    const StepLaunch& L = step_cfg(b, k);
+    const auto& T = b->tiles[k];
+    StepHostArgs a = step_args(b, dt_ptr, dt_val);
+    if (b->mode == MHD_MODE_PER_PATCH) {
+        for (int p = 0; p < b->npatch; ++p) {
+            a.tiles = T.d_nat + T.first[p];
+            a.ntiles = T.count[p];
+            a.dynamic = 0;
+            CK(L.launch(&a, T.count[p], b->stream));
+            b->launches++;
+        }
+    } else if (b->mode == MHD_MODE_BUNCHED) {
+        a.tiles = T.d_nat;
+        a.ntiles = T.n;
+        a.dynamic = 0;
+        CK(L.launch(&a, T.n, b->stream));
+        b->launches++;
+    } else {
+        int occ = 1;
+        CK(L.occupancy(&occ));
+        occ = std::max(occ, 1);
+        const int grid = std::min(T.n, b->nsm * occ);
+        a.tiles = T.d_lpt;
+        a.ntiles = T.n;
+        a.dynamic = 1;
+        CK(L.launch(&a, grid, b->stream));
+        b->launches++;
+    }
+    b->cur = 1 - b->cur;
+    return MHD_OK;
+}
+
+int read_error(mhd_bunch* b, int* code, char* msg, size_t len) {
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream));
+    int c = MHD_OK;
+    std::string m;
+    if (h & ERR_BOUNDS) {
+        c = MHD_EBOUNDS;
+        m = "device index outside the patch table";
+    } else if (h & ERR_TIMEOUT) {
+        c = MHD_ETIMEOUT;
+        m = "a bounded device wait ran out";
+    } else if (h & ERR_PHYS) {
+        c = MHD_EPHYS;
+        m = "non-physical state (rho <= 0 or non-finite value)";
+    }
+    if (code) *code = c;
+    if (msg && len) {
+        std::snprintf(msg, len, "%s", m.c_str());
+    }
+    if (c != MHD_OK) g_err = m;
+    return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_bunch_create(int nx, int ny, int nz, int guard, int nvar, int npatch, int real_bytes, mhd_bunch** out) {
+    if (npatch <= 0) return fail(MHD_EINVAL, "npatch must be positive");
+    std::vector<int32_t> pn(3 * (size_t)npatch);
+    for (int p = 0; p < npatch; ++p) {
+        pn[3 * p] = nx;
+        pn[3 * p + 1] = ny;
+        pn[3 * p + 2] = nz;
+    }
+    return common_create(pn.data(), npatch, guard, nvar, real_bytes, out);
+}
+
+int mhd_bunch_create_ragged(const int32_t* patch_n, int npatch, int guard, int nvar, int real_bytes,
+                            mhd_bunch** out) {
+    return common_create(patch_n, npatch, guard, nvar, real_bytes, out);
+}
+
+int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patch_origin,
+                           const int64_t domain_cells[3], const int32_t bc[6]) {
+    if (!b || !dx || !patch_origin || !domain_cells || !bc) return fail(MHD_EINVAL, "NULL argument");
+    for (int d = 0; d < 3; ++d) {
+        if (!(dx[d] > 0) || !std::isfinite(dx[d])) return fail(MHD_EINVAL, "dx must be positive");
+        if (domain_cells[d] < 1 || domain_cells[d] > (1LL << 30)) return fail(MHD_EINVAL, "bad domain size");
+        const bool act = domain_cells[d] > 1;
+        if (act != (b->pn[d] > 1)) return fail(MHD_EINVAL, "collapsed axes of the box and the patches differ");
+    }
+    for (int k = 0; k < 6; ++k)
+        if (bc[k] != MHD_BC_PERIODIC && bc[k] != MHD_BC_OUTFLOW) return fail(MHD_EINVAL, "bad boundary kind");
+    // owner-map block = gcd of every patch size and origin and the box extent, per axis
+    int64_t bs[3];
+    for (int d = 0; d < 3; ++d) {
+        int64_t g = domain_cells[d];
+        for (int p = 0; p < b->npatch; ++p) {
+            g = gcd64(g, b->pn[3 * p + d]);
+            g = gcd64(g, patch_origin[3 * p + d]);
+        }
+        bs[d] = std::max<int64_t>(g, 1);
+    }
+    int64_t M[3];
+    for (int d = 0; d < 3; ++d) M[d] = domain_cells[d] / bs[d];
+    const int64_t ncell = M[0] * M[1] * M[2];
+    if (ncell > (1LL << 28)) return fail(MHD_EINVAL, "owner map too large");
+    std::vector<int> owner((size_t)ncell, -1);
+    for (int p = 0; p < b->npatch; ++p) {
+        int64_t lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = patch_origin[3 * p + d];
+            hi[d] = lo[d] + b->pn[3 * p + d];
+            if (lo[d] < 0 || hi[d] > domain_cells[d]) return fail(MHD_EINVAL, "patch outside the box");
+        }
+        for (int64_t z = lo[2] / bs[2]; z < hi[2] / bs[2]; ++z)
+            for (int64_t y = lo[1] / bs[1]; y < hi[1] / bs[1]; ++y)
+                for (int64_t x = lo[0] / bs[0]; x < hi[0] / bs[0]; ++x) {
+                    int& o = owner[(size_t)((z * M[1] + y) * M[0] + x)];
+                    if (o != -1) return fail(MHD_EINVAL, "patches overlap");
+                    o = p;
+                }
+    }
+    for (int o : owner)
+        if (o < 0) return fail(MHD_EINVAL, "patches do not cover the box");
+    release_graph(b);
+    cudaFree(b->d_owner);
+    b->d_owner = nullptr;
+    CK(cudaMalloc(&b->d_owner, sizeof(int) * owner.size()));
+    CK(cudaMemcpy(b->d_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice));
+    for (int d = 0; d < 3; ++d) {
+        b->dx[d] = dx[d];
+        b->domain[d] = domain_cells[d];
+        b->fg.N[d] = (int)domain_cells[d];
+        b->fg.bs[d] = (int)bs[d];
+        b->fg.M[d] = (int)M[d];
+        b->fg.bc[d][0] = bc[2 * d];
+        b->fg.bc[d][1] = bc[2 * d + 1];
+    }
+    for (int k = 0; k < 6; ++k) b->bc[k] = bc[k];
+    b->fg.owner = b->d_owner;
+    b->origin.assign(patch_origin, patch_origin + 3 * b->npatch);
+    for (int p = 0; p < b->npatch; ++p) {
+        b->hp[p].ox = (int)patch_origin[3 * p];
+        b->hp[p].oy = (int)patch_origin[3 * p + 1];
+        b->hp[p].oz = (int)patch_origin[3 * p + 2];
+    }
+    CK(cudaMemcpy(b->d_patches, b->hp.data(), sizeof(PatchDev) * b->npatch, cudaMemcpyHostToDevice));
+    int rc = build_tiles(b);
+    if (rc != MHD_OK) return rc;
+    b->have_geom = true;
+    return MHD_OK;
+}
+
+int mhd_bunch_set_params(mhd_bunch* b, double gamma, double courant, int limiter) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(MHD_EINVAL, "gamma must be > 1");
+    if (!(courant > 0.0) || !std::isfinite(courant)) return fail(MHD_EINVAL, "courant must be > 0");
+    if (limiter != MHD_LIMITER_MINMOD && limiter != MHD_LIMITER_MC) return fail(MHD_EINVAL, "bad limiter");
+    release_graph(b);
+    b->gamma = gamma;
+    b->courant = courant;
+    b->limiter = limiter;
+    return MHD_OK;
+}
+
+int mhd_bunch_state_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) {
+    if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
+    *bytes = b->state_bytes;
+    if (patch_offsets) std::copy(b->offs.begin(), b->offs.end(), patch_offsets);
+    return MHD_OK;
+}
+
+int mhd_bunch_bind(mhd_bunch* b, void* state, void* state_next, void* cuda_stream) {
+    if (!b || !state || !state_next) return fail(MHD_EINVAL, "NULL argument");
+    if (state == state_next) return fail(MHD_EINVAL, "state and state_next must differ");
+    if ((reinterpret_cast<uintptr_t>(state) & 15) || (reinterpret_cast<uintptr_t>(state_next) & 15))
+        return fail(MHD_EINVAL, "state buffers must be 16-byte aligned");
+    release_graph(b);
+    b->buf[0] = state;
+    b->buf[1] = state_next;
+    b->cur = 0;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    return MHD_OK;
+}
+
+int mhd_bunch_current(const mhd_bunch* b, void** state) {
+    if (!b || !state) return fail(MHD_EINVAL, "NULL argument");
+    *state = b->buf[b->cur];
+    return MHD_OK;
+}
+
+int mhd_bunch_fill_guards(mhd_bunch* b) {
+    int rc = ready(b);
+    if (rc) return rc;
+    return do_fill(b);
+}
+
+int mhd_bunch_cfl_dt_device(mhd_bunch* b, void* dt_dev) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
+    return do_cfl(b, static_cast<double*>(dt_dev));
+}
+
+int mhd_bunch_cfl_dt(mhd_bunch* b, double* dt_host) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!dt_host) return fail(MHD_EINVAL, "dt_host is NULL");
+    rc = do_cfl(b, b->d_dt);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(dt_host, b->d_dt, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    return code;
+}
+
+int mhd_bunch_step(mhd_bunch* b, double dt) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!(dt >= 0) || !std::isfinite(dt)) return fail(MHD_EINVAL, "dt must be finite and >= 0");
+    return do_step(b, nullptr, dt);
+}
+
+int mhd_bunch_step_device_dt(mhd_bunch* b, const void* dt_dev) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
+    return do_step(b, static_cast<const double*>(dt_dev), 0.0);
+}
+
+int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_PERSISTENT) return fail(MHD_EINVAL, "bad mode");
+    if (config < -1 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
+    release_graph(b);
+    b->mode = mode;
+    b->config = config;
+    return MHD_OK;
+}
+
+int mhd_bunch_num_configs(const mhd_bunch* b, int* nconfig) {
+    if (!b || !nconfig) return fail(MHD_EINVAL, "NULL argument");
+    *nconfig = (int)b->cfg_index.size();
+    return MHD_OK;
+}
+
+int mhd_bunch_config_info(const mhd_bunch* b, int config, int* tile_x, int* tile_y, int* threads) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (config < 0 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
+    const StepLaunch& L = step_cfg(b, config);
+    if (tile_x) *tile_x = L.tx;
+    if (tile_y) *tile_y = L.ty;
+    if (threads) *threads = L.nt;
+    return MHD_OK;
+}
+
+int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
+    int rc = ready(b);
+    if (rc) return rc;
+    const int n = (int)b->cfg_index.size();
+    if (n == 0) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
+    // cache key: device name, precision, dimensionality and the multiset of patch sizes
+    cudaDeviceProp prop;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaGetDeviceProperties(&prop, dev));
+    std::ostringstream key;
+    key << prop.name << "|r" << b->rb << "|d" << b->ndim << "|m" << b->mode;
+    {
+        std::vector<int> sizes;
+        for (int p = 0; p < b->npatch; ++p) sizes.push_back(b->pn[3 * p] * 10000 + b->pn[3 * p + 1] * 100 + b->pn[3 * p + 2]);
+        std::sort(sizes.begin(), sizes.end());
+        int64_t h = 1469598103934665603LL;
+        for (int s : sizes) h = (h ^ s) * 1099511628211LL;
+        key << "|p" << b->npatch << "|h" << (uint64_t)h;
+    }
+    std::string k = key.str();
+    for (auto& ch : k)
+        if (ch == ' ') ch = '_';
+    if (cache_path) {
+        std::ifstream f(cache_path);
+        std::string kk;
+        int idx;
+        while (f >> kk >> idx)
+            if (kk == k && idx >= 0 && idx < n) {
+                release_graph(b);
+                b->config = idx;
+                if (chosen) *chosen = idx;
+                return MHD_OK;
+            }
+    }
+    // time every configuration on the bound state, then restore it
+    void* save = nullptr;
+    CK(cudaMalloc(&save, b->state_bytes));
+    const int cur0 = b->cur;
+    cudaError_t e = cudaMemcpyAsync(save, b->buf[cur0], b->state_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e != cudaSuccess) {
+        cudaFree(save);
+        return fail(MHD_ECUDA, cudaGetErrorString(e));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int keep = b->config;
+    float best = 1e30f;
+    int besti = 0;
+    rc = do_fill(b);
+    for (int c = 0; c < n && rc == MHD_OK; ++c) {
+        b->config = c;
+        // dt = 0 keeps the state unchanged in value; the work is the same as a real step
+        for (int w = 0; w < 2 && rc == MHD_OK; ++w) {
+            rc = do_fill(b);
+            if (!rc) rc = do_step(b, nullptr, 0.0);
+        }
+        if (rc) break;
+        e = cudaEventRecord(e0, b->stream);
+        for (int w = 0; w < 4 && rc == MHD_OK; ++w) {
+            rc = do_fill(b);
+            if (!rc) rc = do_step(b, nullptr, 0.0);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(MHD_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            besti = c;
+        }
+    }
+    // restore the state into the buffer that held it
+    b->cur = cur0;
+    e = cudaMemcpyAsync(b->buf[cur0], save, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(save);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        b->config = keep;
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(MHD_ECUDA, cudaGetErrorString(e));
+    release_graph(b);
+    b->config = besti;
+    if (chosen) *chosen = besti;
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << k << " " << besti << "\n";
+    }
+    return MHD_OK;
+}
+
+int mhd_bunch_graph_capture(mhd_bunch* b, int nsteps, void* dt_dev) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (nsteps <= 0) return fail(MHD_EINVAL, "nsteps must be positive");
+    release_graph(b);
+    const int cur0 = b->cur;
+    const int64_t l0 = b->launches;
+    // an even sequence returns to its starting buffer: one graph; an odd one swaps, so a
+    // second graph starting from the other buffer is captured as well
+    const int ngraphs = (nsteps & 1) ? 2 : 1;
+    for (int gi = 0; gi < ngraphs; ++gi) {
+        b->cur = gi == 0 ? cur0 : 1 - cur0;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < nsteps && rc == MHD_OK; ++s) {
+            double* dt = dt_dev ? static_cast<double*>(dt_dev) + s : b->d_dt;
+            rc = do_fill(b);
+            if (!rc) rc = do_cfl(b, dt);
+            if (!rc) rc = do_step(b, dt, 0.0);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            b->cur = cur0;
+            b->launches = l0;
+            release_graph(b);
+            return rc ? rc : fail(MHD_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&b->gexec[gi], g, 0);
+        b->graph[gi] = g;
+        if (e != cudaSuccess) {
+            b->cur = cur0;
+            b->launches = l0;
+            release_graph(b);
+            return fail(MHD_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    b->cur = cur0;
+    b->launches = l0;
+    b->graph_steps = nsteps;
+    b->graph_start = cur0;
+    return MHD_OK;
+}
+
+int mhd_bunch_graph_launch(mhd_bunch* b) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!b->gexec[0]) return fail(MHD_ESTATE, "no captured graph");
+    const int gi = (b->cur == b->graph_start) ? 0 : 1;
+    if (!b->gexec[gi]) return fail(MHD_ESTATE, "current buffer differs from the captured one");
+    CK(cudaGraphLaunch(b->gexec[gi], b->stream));
+    size_t nn = 0;
+    cudaGraphGetNodes(b->graph[gi], nullptr, &nn);
+    b->launches += (int64_t)nn;
+    if (b->graph_steps & 1) b->cur = 1 - b->cur;
+    return MHD_OK;
+}
+
+int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t_out) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!host_state || nsteps < 0) return fail(MHD_EINVAL, "bad argument");
+    if (nsteps > b->d_dts_cap) {
+        cudaFree(b->d_dts);
+        b->d_dts = nullptr;
+        CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
+        b->d_dts_cap = nsteps;
+    }
+    CK(cudaMemcpyAsync(b->buf[b->cur], host_state, b->state_bytes, cudaMemcpyHostToDevice, b->stream));
+    for (int s = 0; s < nsteps; ++s) {
+        rc = do_fill(b);
+        if (!rc) rc = do_cfl(b, b->d_dts + s);
+        if (!rc) rc = do_step(b, b->d_dts + s, 0.0);
+        if (rc) return rc;
+    }
+    std::vector<double> dts(nsteps);
+    if (nsteps) CK(cudaMemcpyAsync(dts.data(), b->d_dts, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(host_state, b->buf[b->cur], b->state_bytes, cudaMemcpyDeviceToHost, b->stream));
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
+    return code;
+}
+
+int mhd_bunch_get_error(mhd_bunch* b, int* code, char* msg, size_t len) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    return read_error(b, code, msg, len);
+}
+
+int mhd_bunch_launch_count(const mhd_bunch* b, int64_t* count) {
+    if (!b || !count) return fail(MHD_EINVAL, "NULL argument");
+    *count = b->launches;
+    return MHD_OK;
+}
+
+void mhd_bunch_destroy(mhd_bunch* b) {
+    if (!b) return;
+    release_graph(b);
+    free_tiles(b);
+    cudaFree(b->d_patches);
+    cudaFree(b->d_owner);
+    cudaFree(b->d_work);
+    cudaFree(b->d_partial);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_dt);
+    cudaFree(b->d_dts);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+const char* mhd_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, const void* lam_next, void* lam) {
+    (void)dt;
+    (void)U_n;
+    (void)lam_next;
+    (void)lam;
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    return fail(MHD_ESTATE, "adjoint kernels not built in this version");
+}

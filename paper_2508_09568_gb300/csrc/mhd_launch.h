@@ -1,0 +1,52 @@
+// Host-side launch table of the per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "mhd_common.cuh"
+
+namespace mhd {
+
+// One compiled configuration of the fused step kernel.
+struct StepLaunch {
+    int ndim, tx, ty, nt;
+    size_t smem;
+    cudaError_t (*prepare)();                                   // opt in to large smem
+    cudaError_t (*occupancy)(int* blocks_per_sm);
+    cudaError_t (*launch)(const void* args, int grid, cudaStream_t s);
+};
+
+// Kernel entry points of one precision (R = float or double).
+struct PrecisionKernels {
+    const StepLaunch* step;
+    int nstep;
+    cudaError_t (*fill)(void* U, const PatchDev* patches, int npatch, const FillGeom& fg, unsigned* err,
+                        cudaStream_t s);
+    // partial: at least cfl_grid reals; counter: one zeroed unsigned
+    cudaError_t (*cfl)(const void* U, const PatchDev* patches, int npatch, double gamma, double courant,
+                       const double dxi[3], const int act[3], void* partial, int grid, unsigned* counter,
+                       double* dt_out, unsigned* err, cudaStream_t s);
+};
+
+const PrecisionKernels& kernels_f32();
+const PrecisionKernels& kernels_f64();
+
+// arguments of the step kernel in a precision-independent form (converted per precision)
+struct StepHostArgs {
+    const void* U;
+    void* Unew;
+    const PatchDev* patches;
+    const int4* tiles;
+    int ntiles;
+    int dynamic;
+    int* work;
+    const double* dt_ptr;
+    double dt_val;
+    double gamma, eps;
+    double dxi[3];
+    int limiter;
+    unsigned* err;
+};
+
+}  // namespace mhd
