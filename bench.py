@@ -193,8 +193,12 @@ def run_ours(args, ws, rank, local):
     with torch.cuda.stream(b.stream):
         b.current().copy_(host, non_blocking=True)
     b.stream.synchronize()
-    b.set_mode(capi.MHD_MODE_PERSISTENT, -1)
-    cfg = b.autotune(None)
+    if args.config >= 0:
+        cfg = args.config
+        b.set_mode(capi.MHD_MODE_PERSISTENT, cfg)
+    else:
+        b.set_mode(capi.MHD_MODE_PERSISTENT, -1)
+        cfg = b.autotune(None)
     tile = b.config_info(cfg)
 
     # ---- timed region: graph replay of (fill -> CFL dt -> step), K steps
@@ -240,35 +244,39 @@ def run_ours(args, ws, rank, local):
         raise RuntimeError(f"device error during the benchmark: {msg}")
 
     # ---- the plain path: one launch per patch (same kernel), eager
-    kp = max(2, min(args.steps, 4))
-    b.set_mode(capi.MHD_MODE_PER_PATCH, cfg)
-    b.fill_guards()
-    b.cfl_dt_device(dt_dev)
-    b.step_device_dt(dt_dev)
-    b.stream.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(b.stream)
-    for _ in range(kp):
+    kp = 0 if args.no_plain else max(2, min(args.steps, 4))
+    plain = None
+    if kp:
+        b.set_mode(capi.MHD_MODE_PER_PATCH, cfg)
         b.fill_guards()
         b.cfl_dt_device(dt_dev)
         b.step_device_dt(dt_dev)
-    p1.record(b.stream)
-    b.stream.synchronize()
-    plain = cells * kp / (p0.elapsed_time(p1) * 1e-3)
-    b.set_mode(capi.MHD_MODE_PERSISTENT, cfg)
+        b.stream.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(b.stream)
+        for _ in range(kp):
+            b.fill_guards()
+            b.cfl_dt_device(dt_dev)
+            b.step_device_dt(dt_dev)
+        p1.record(b.stream)
+        b.stream.synchronize()
+        plain = cells * kp / (p0.elapsed_time(p1) * 1e-3)
+        b.set_mode(capi.MHD_MODE_PERSISTENT, cfg)
 
     # ---- end to end through the C ABI on host buffers (H2D + fill + dt + step + D2H per step)
-    ke = max(1, min(args.steps, 3))
-    b.advance_host(host, 1)
-    torch.cuda.synchronize()
-    barrier(ws)
-    t0 = time.perf_counter()
-    for _ in range(ke):
+    e2e = None
+    if not args.no_e2e:
+        ke = max(1, min(args.steps, 3))
         b.advance_host(host, 1)
-    te = time.perf_counter() - t0
-    te = allmax(te, ws)
-    e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": b.nbytes,
-           "d2h_bytes_per_step": b.nbytes}
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            b.advance_host(host, 1)
+        te = time.perf_counter() - t0
+        te = allmax(te, ws)
+        e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": b.nbytes,
+               "d2h_bytes_per_step": b.nbytes}
 
     # ---- roofline of the dominant kernel (the fused step)
     step_s = t_step * 1e-3
@@ -315,6 +323,9 @@ def main():
     ap.add_argument("--ncell", type=int, default=512)
     ap.add_argument("--patch", type=int, default=32)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-launch-per-patch comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--config", type=int, default=-1, help="tile configuration (default: autotune)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

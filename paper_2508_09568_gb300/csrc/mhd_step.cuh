@@ -32,11 +32,11 @@ struct StepCfg {
     static constexpr int LSZ = LX * LY;
     static constexpr int NWV = 11;          // 8 primitives + 3 face fields
     static constexpr int NWSLOT = AZ ? 3 : 1;
-    // prep: i in [-1, TX+1], j in [-1, TY+1]
+    // prep: i in [-1, TX], j in [-1, TY]
     static constexpr int POX = 1, POY = AY ? 1 : 0;
-    static constexpr int PX = TX + 3, PY = AY ? TY + 3 : 1;
+    static constexpr int PX = TX + 2, PY = AY ? TY + 2 : 1;
     static constexpr int PSZ = PX * PY;
-    static constexpr int NPV = 41;          // Wh(8) + dW(24) + bh(3) + face slopes(6)
+    static constexpr int NPV = 38;          // Wh(8) + dW(21) + bh(3) + face slopes(6)
     static constexpr int NPSLOT = AZ ? 2 : 1;
     // flux buffers
     static constexpr int FXN = (TX + 1) * TY;
@@ -51,17 +51,25 @@ struct StepCfg {
     static constexpr size_t SMEM_REALS = (size_t)NWSLOT * NWV * LSZ + (size_t)NPSLOT * NPV * PSZ +
                                          (size_t)NINB * INB + (size_t)NZB * ZB;
     static constexpr size_t SMEM_BYTES = SMEM_REALS * sizeof(R) + 16;
-    // work segments of the flux stage, each padded to a warp multiple
+    // Work segments of the flux stage.  Each walks rows of the prep pitch PX (idle lanes
+    // at the row ends) so that a warp's shared-memory reads of the prep arrays are
+    // contiguous (no bank conflicts); each is padded to a warp multiple.
     static constexpr int pad32(int n) { return (n + 31) / 32 * 32; }
-    static constexpr int S_FX = pad32(FXN), S_FY = pad32(FYN), S_EZ = pad32(EZN);
-    static constexpr int S_FZ = pad32(FZN), S_EX = pad32(EXN), S_EY = pad32(EYN);
+    static constexpr int RFX = TY, RFY = AY ? TY + 1 : 0, REZ = AY ? TY + 1 : 1;
+    static constexpr int RFZ = AZ ? TY : 0, REX = AY ? TY + 1 : 0, REY = TY;
+    static constexpr int S_FX = pad32(RFX * PX), S_FY = pad32(RFY * PX), S_EZ = pad32(REZ * PX);
+    static constexpr int S_FZ = pad32(RFZ * PX), S_EX = pad32(REX * PX), S_EY = pad32(REY * PX);
+    // update stage rows of pitch TX+1
+    static constexpr int S_UP = TY * (TX + 1);
 };
 
 // prep slot variable indices
 #define PV_WH(k) (k)
-#define PV_DW(d, k) (8 + 8 * (d) + (k))
-#define PV_BH(c) (32 + (c))
-#define PV_FS(c, k) (35 + 2 * (c) + (k))   // slope of face field c along (c+k+1)%3
+// slope of primitive k along d (the slope of the normal field component along its own
+// axis is never used and not stored)
+#define PV_DW(d, k) (8 + 7 * (d) + ((k) < 5 + (d) ? (k) : (k) - 1))
+#define PV_BH(c) (29 + (c))
+#define PV_FS(c, k) (32 + 2 * (c) + (k))   // slope of face field c along (c+k+1)%3
 
 template <typename R, typename C>
 struct StepSmem {
@@ -276,7 +284,8 @@ __device__ __forceinline__ void prep_cell(const PrepCtx<R, C>& X, int i, int j, 
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) Pslot[PV_DW(d, k) * C::PSZ + pid] = dW[d][k];
+        for (int k = 0; k < 8; ++k)
+            if (k != 5 + d) Pslot[PV_DW(d, k) * C::PSZ + pid] = dW[d][k];
     Pslot[PV_BH(0) * C::PSZ + pid] = bxh0;
     Pslot[PV_BH(1) * C::PSZ + pid] = byh0;
     Pslot[PV_BH(2) * C::PSZ + pid] = bzh0;
@@ -359,8 +368,64 @@ struct StepArgs {
     unsigned* err;
 };
 
-template <typename R, int NDIM, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
+// a9 for one plane u of the tile: conservative update and constrained transport (Eq. 12)
+// from the in-plane buffer of plane u and the inter-plane buffers of levels u-1/2, u+1/2.
+// Threads walk rows of pitch TX+1 (one idle lane per row) so flux reads are contiguous.
+template <typename R, typename C>
+__device__ __forceinline__ void stage_update(const StepSmem<R, C>& S, const R* __restrict__ U, R* __restrict__ Unew,
+                                             const PatchDev& pt, int x0, int y0, int u, int wx, int wy, R dtdx0,
+                                             R dtdx1, R dtdx2, unsigned* err) {
+    const R* IB = S.I(C::AZ ? (u & 1) : 0);
+    const R* Fx = IB;
+    const R* Fy = IB + 5 * C::FXN;
+    const R* Ez = Fy + 5 * C::FYN;
+    const R* ZL = S.Z(C::AZ ? (u & 1) : 0);        // level u-1/2
+    const R* ZH = S.Z(C::AZ ? ((u + 1) & 1) : 0);  // level u+1/2
+    const R* FzL = ZL;
+    const R* FzH = ZH;
+    const R* ExL = ZL + 5 * C::FZN;
+    const R* ExH = ZH + 5 * C::FZN;
+    const R* EyL = ExL + C::EXN;
+    const R* EyH = ExH + C::EXN;
+    const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
+    for (int w = threadIdx.x; w < C::S_UP; w += C::NT) {
+        const int i = w % (C::TX + 1), j = w / (C::TX + 1);
+        if (i >= wx || j >= wy) continue;
+        const int x = x0 + i + pt.gx, y = C::AY ? y0 + j + pt.gy : 0, z = u + pt.gz;
+        const int64_t o = pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+        const int fx = j * (C::TX + 1) + i;   // x-faces, Ez, Ey: pitch TX+1
+        const int fy = j * C::TX + i;         // y-faces, z-faces, Ex: pitch TX
+        R du[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            R d = dtdx0 * (Fx[v * C::FXN + fx + 1] - Fx[v * C::FXN + fx]);
+            if (C::AY) d += dtdx1 * (Fy[v * C::FYN + fy + C::TX] - Fy[v * C::FYN + fy]);
+            if (C::AZ) d += dtdx2 * (FzH[v * C::FZN + fy] - FzL[v * C::FZN + fy]);
+            du[v] = -d;
+        }
+        R dbx = R(0), dby, dbz;
+        if (C::AY) dbx += dtdx1 * (Ez[fx + (C::TX + 1)] - Ez[fx]);
+        if (C::AZ) dbx -= dtdx2 * (EyH[fx] - EyL[fx]);
+        dby = -dtdx0 * (Ez[fx + 1] - Ez[fx]);
+        if (C::AZ) dby += dtdx2 * (ExH[fy] - ExL[fy]);
+        dbz = dtdx0 * (EyL[fx + 1] - EyL[fx]);
+        if (C::AY) dbz -= dtdx1 * (ExL[fy + C::TX] - ExL[fy]);
+        const R* Ub = U + o;
+        R* Un = Unew + o;
+        R nv[8];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) nv[v] = Ub[v * vol] + du[v];
+        nv[5] = Ub[5 * vol] + dbx;
+        nv[6] = Ub[6 * vol] + dby;
+        nv[7] = Ub[7 * vol] + dbz;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) Un[v * vol] = nv[v];
+        if (!(nv[0] > R(0)) || !isfinite((double)nv[4])) atomicOr(err, ERR_PHYS);
+    }
+}
+
+template <typename R, int NDIM, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     using C = StepCfg<R, NDIM, TX, TY, NT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
@@ -373,7 +438,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
     __shared__ int s_tile;
 
     const double dtd = a.dt_ptr ? *a.dt_ptr : a.dt_val;
-    const R dt = R(dtd), hdt = R(0.5 * dtd);
+    const R hdt = R(0.5 * dtd);
     const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0), gm1i = R(1.0 / (a.gamma - 1.0));
     const R eps = R(a.eps);
     const R dtdx0 = R(dtd * a.dxi[0]), dtdx1 = R(dtd * a.dxi[1]), dtdx2 = R(dtd * a.dxi[2]);
@@ -392,7 +457,10 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
         const int x0 = tl.y, y0 = tl.z;
         const int wx = min(C::TX, pt.nx - x0), wy = C::AY ? min(C::TY, pt.ny - y0) : 1;
         const int nz = C::AZ ? pt.nz : 1;
-        const int niter = C::AZ ? nz + 4 : 1;
+        // 3D: iteration s loads plane s-2, prepares plane s-3 (fluxes of that plane and
+        // of the level below it) and updates plane s-5 (whose last inter-plane level was
+        // computed in iteration s-1); one extra iteration finishes the last update.
+        const int niter = C::AZ ? nz + 5 : 1;
 
         PrepCtx<R, C> X;
         X.hdt = hdt;
@@ -405,21 +473,26 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
         for (int s = 0; s < niter; ++s) {
             const int m = C::AZ ? s - 2 : 0;     // plane loaded
             const int c = C::AZ ? s - 3 : 0;     // plane prepared
-            // ---- load + convert plane m
+            // ---- load plane m (+ the update of plane s-5, which reads only flux buffers)
             R* Wm_slot = S.W(C::AZ ? (m + 3) % 3 : 0);
-            stage_load<R, C>(a.U, pt, x0, y0, m, Wm_slot, bznext);
+            if (!C::AZ || m <= nz + 1) stage_load<R, C>(a.U, pt, x0, y0, m, Wm_slot, bznext);
+            if (C::AZ && s >= 5)
+                stage_update<R, C>(S, a.U, a.Unew, pt, x0, y0, s - 5, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
             __syncthreads();
+            if (C::AZ && m > nz + 1) break;      // the last update is done
             stage_convert<R, C>(Wm_slot, bznext, gm1);
             __syncthreads();
-            // ---- prep plane c
+            // ---- prep plane c: threads walk rows of the W-ring pitch LX so that the
+            // stencil reads of the W ring are contiguous; active lanes cover i in [-1, TX]
             if (c >= -1) {
                 X.W0 = S.W(C::AZ ? (c + 3) % 3 : 0);
                 X.Wm = S.W(C::AZ ? (c + 2) % 3 : 0);
                 X.Wp = S.W(C::AZ ? (c + 4) % 3 : 0);
                 R* Ps = S.P(C::AZ ? (c + 2) & 1 : 0);
-                for (int w = threadIdx.x; w < C::PSZ; w += C::NT) {
-                    const int i = w % C::PX - C::POX, j = w / C::PX - C::POY;
-                    prep_cell<R, C>(X, i, j, Ps, w);
+                for (int w = threadIdx.x; w < C::PY * C::LX; w += C::NT) {
+                    const int i = w % C::LX - C::LOX, j = w / C::LX - C::POY;
+                    if (i < -1 || i > C::TX) continue;
+                    prep_cell<R, C>(X, i, j, Ps, pidx<C>(i, j));
                 }
             }
             __syncthreads();
@@ -439,37 +512,40 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
                 constexpr int TOT = C::S_FX + C::S_FY + C::S_EZ + C::S_FZ + C::S_EX + C::S_EY;
                 for (int w = threadIdx.x; w < TOT; w += C::NT) {
                     int r = w;
-                    if (r < C::S_FX) {
-                        if (inplane && r < C::FXN) {   // x-face i-1/2 of cell (i, j)
-                            const int i = r % (C::TX + 1), j = r / (C::TX + 1);
+                    if (r < C::S_FX) {   // x-face i-1/2 of cell (i, j): i in [0, TX], j in [0, TY)
+                        const int i = r % C::PX, j = r / C::PX;
+                        if (inplane && i <= C::TX && j < C::RFX) {
                             R F[5];
                             face_flux<R, C>(P0, pidx<C>(i - 1, j), P0, pidx<C>(i, j), 0, gamma, gm1i, eps, F);
+                            const int o = j * (C::TX + 1) + i;
 #pragma unroll
-                            for (int v = 0; v < 5; ++v) Fx[v * C::FXN + r] = F[v];
+                            for (int v = 0; v < 5; ++v) Fx[v * C::FXN + o] = F[v];
                         }
                         continue;
                     }
                     r -= C::S_FX;
-                    if (r < C::S_FY) {
-                        if (C::AY && inplane && r < C::FYN) {   // y-face j-1/2 of cell (i, j)
-                            const int i = r % C::TX, j = r / C::TX;
+                    if (r < C::S_FY) {   // y-face j-1/2 of cell (i, j): i in [0, TX), j in [0, TY]
+                        const int i = r % C::PX - 1, j = r / C::PX;
+                        if (C::AY && inplane && i >= 0 && i < C::TX && j < C::RFY) {
                             R F[5];
                             face_flux<R, C>(P0, pidx<C>(i, j - 1), P0, pidx<C>(i, j), 1, gamma, gm1i, eps, F);
+                            const int o = j * C::TX + i;
 #pragma unroll
-                            for (int v = 0; v < 5; ++v) Fy[v * C::FYN + r] = F[v];
+                            for (int v = 0; v < 5; ++v) Fy[v * C::FYN + o] = F[v];
                         }
                         continue;
                     }
                     r -= C::S_FY;
-                    if (r < C::S_EZ) {
-                        if (inplane && r < C::EZN) {   // Ez at (i-1/2, j-1/2)
-                            const int i = r % (C::TX + 1), j = r / (C::TX + 1);
+                    if (r < C::S_EZ) {   // Ez at (i-1/2, j-1/2): i in [0, TX], j in [0, TY]
+                        const int i = r % C::PX, j = r / C::PX;
+                        if (inplane && i <= C::TX && j < C::REZ) {
                             const int jm = C::AY ? j - 1 : j;
                             // cells: SW=(i-1,j-1) RT, SE=(i,j-1) LT, NW=(i-1,j) RB, NE=(i,j) LB
                             const int pSW = pidx<C>(i - 1, jm), pSE = pidx<C>(i, jm);
                             const int pNW = pidx<C>(i - 1, j), pNE = pidx<C>(i, j);
-                            // Ba = Bx face on side sa (+ slope along y), Bb = By face on side sb (+ slope along x)
-                            // the x-face between i-1 and i is the low face of cell i; By faces: low face of row j
+                            // Ba = Bx face on side sa (+ slope along y): the x-face between
+                            // cells i-1 and i is the low face of cell i; Bb = By face on side
+                            // sb (+ slope along x): the low y-face of row j
                             const R bxS = pv<R, C>(P0, PV_BH(0), pSE), bxN = pv<R, C>(P0, PV_BH(0), pNE);
                             const R sxS = pv<R, C>(P0, PV_FS(0, 0), pSE), sxN = pv<R, C>(P0, PV_FS(0, 0), pNE);
                             const R byW = pv<R, C>(P0, PV_BH(1), pNW), byE = pv<R, C>(P0, PV_BH(1), pNE);
@@ -478,30 +554,31 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
                             const Corner<R> SE = corner<R, C>(P0, pSE, 2, R(-1), R(1), bxS, sxS, byE, syE);
                             const Corner<R> NW = corner<R, C>(P0, pNW, 2, R(1), R(-1), bxN, sxN, byW, syW);
                             const Corner<R> NE = corner<R, C>(P0, pNE, 2, R(-1), R(-1), bxN, sxN, byE, syE);
-                            Ez[r] = emf2d(SW, SE, NW, NE, gamma);
+                            Ez[j * (C::TX + 1) + i] = emf2d(SW, SE, NW, NE, gamma);
                         }
                         continue;
                     }
                     r -= C::S_EZ;
-                    if (r < C::S_FZ) {
-                        if (C::AZ && r < C::FZN) {   // z-face c-1/2 of cell (i, j)
-                            const int i = r % C::TX, j = r / C::TX;
+                    if (r < C::S_FZ) {   // z-face c-1/2 of cell (i, j): i in [0, TX), j in [0, TY)
+                        const int i = r % C::PX - 1, j = r / C::PX;
+                        if (C::AZ && i >= 0 && i < C::TX && j < C::RFZ) {
                             const int p = pidx<C>(i, j);
                             R F[5];
                             face_flux<R, C>(Pm, p, P0, p, 2, gamma, gm1i, eps, F);
+                            const int o = j * C::TX + i;
 #pragma unroll
-                            for (int v = 0; v < 5; ++v) Fz[v * C::FZN + r] = F[v];
+                            for (int v = 0; v < 5; ++v) Fz[v * C::FZN + o] = F[v];
                         }
                         continue;
                     }
                     r -= C::S_FZ;
-                    if (r < C::S_EX) {
-                        if (C::AY && r < C::EXN) {   // Ex at (i, j-1/2, c-1/2): a = y, b = z
-                            const int i = r % C::TX, j = r / C::TX;
+                    if (r < C::S_EX) {   // Ex at (i, j-1/2, c-1/2): a = y, b = z; i in [0, TX), j in [0, TY]
+                        const int i = r % C::PX - 1, j = r / C::PX;
+                        if (C::AY && i >= 0 && i < C::TX && j < C::REX) {
                             const int pS = pidx<C>(i, j - 1), pN = pidx<C>(i, j);
                             // SW = (j-1, c-1) corner (+y,+z); SE = (j, c-1) (-y,+z);
                             // NW = (j-1, c) (+y,-z); NE = (j, c) (-y,-z)
-                            // Ba = By face at side sy: low face of row j (shared by j-1 high, j low)
+                            // Ba = By face at side sy: the low y-face of row j (both planes)
                             const R byB = pv<R, C>(Pm, PV_BH(1), pN), byT = pv<R, C>(P0, PV_BH(1), pN);
                             const R syB = pv<R, C>(Pm, PV_FS(1, 0), pN), syT = pv<R, C>(P0, PV_FS(1, 0), pN);
                             // Bb = Bz face at side sz: the face between c-1 and c = low face of plane c
@@ -511,80 +588,35 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(StepArgs<R> a) {
                             const Corner<R> SE = corner<R, C>(Pm, pN, 0, R(-1), R(1), byB, syB, bzE, szE);
                             const Corner<R> NW = corner<R, C>(P0, pS, 0, R(1), R(-1), byT, syT, bzW, szW);
                             const Corner<R> NE = corner<R, C>(P0, pN, 0, R(-1), R(-1), byT, syT, bzE, szE);
-                            Ex[r] = emf2d(SW, SE, NW, NE, gamma);
+                            Ex[j * C::TX + i] = emf2d(SW, SE, NW, NE, gamma);
                         }
                         continue;
                     }
                     r -= C::S_EX;
-                    if (r < C::EYN) {   // Ey at (i-1/2, j, c-1/2): a = z, b = x
-                        const int i = r % (C::TX + 1), j = r / (C::TX + 1);
-                        const int pW = pidx<C>(i - 1, j), pE = pidx<C>(i, j);
-                        // SW = (x=i-1, c-1) corner (+z,+x); SE = (i-1, c) (-z,+x);
-                        // NW = (i, c-1) (+z,-x); NE = (i, c) (-z,-x)
-                        // Ba = Bz face at side sz: low face of plane c (shared); slope along x
-                        const R bzS = pv<R, C>(P0, PV_BH(2), pW), bzN = pv<R, C>(P0, PV_BH(2), pE);
-                        const R szS = pv<R, C>(P0, PV_FS(2, 0), pW), szN = pv<R, C>(P0, PV_FS(2, 0), pE);
-                        // Bb = Bx face at side sx: low face of cell i (shared); slope along z
-                        const R bxW = pv<R, C>(Pm, PV_BH(0), pE), bxE = pv<R, C>(P0, PV_BH(0), pE);
-                        const R sxW = pv<R, C>(Pm, PV_FS(0, 1), pE), sxE = pv<R, C>(P0, PV_FS(0, 1), pE);
-                        const Corner<R> SW = corner<R, C>(Pm, pW, 1, R(1), R(1), bzS, szS, bxW, sxW);
-                        const Corner<R> SE = corner<R, C>(P0, pW, 1, R(-1), R(1), bzS, szS, bxE, sxE);
-                        const Corner<R> NW = corner<R, C>(Pm, pE, 1, R(1), R(-1), bzN, szN, bxW, sxW);
-                        const Corner<R> NE = corner<R, C>(P0, pE, 1, R(-1), R(-1), bzN, szN, bxE, sxE);
-                        Ey[r] = emf2d(SW, SE, NW, NE, gamma);
+                    {   // Ey at (i-1/2, j, c-1/2): a = z, b = x; i in [0, TX], j in [0, TY)
+                        const int i = r % C::PX, j = r / C::PX;
+                        if (i <= C::TX && j < C::REY) {
+                            const int pW = pidx<C>(i - 1, j), pE = pidx<C>(i, j);
+                            // SW = (x=i-1, c-1) corner (+z,+x); SE = (i-1, c) (-z,+x);
+                            // NW = (i, c-1) (+z,-x); NE = (i, c) (-z,-x)
+                            // Ba = Bz face at side sz: low face of plane c (shared); slope along x
+                            const R bzS = pv<R, C>(P0, PV_BH(2), pW), bzN = pv<R, C>(P0, PV_BH(2), pE);
+                            const R szS = pv<R, C>(P0, PV_FS(2, 0), pW), szN = pv<R, C>(P0, PV_FS(2, 0), pE);
+                            // Bb = Bx face at side sx: low face of cell i (shared); slope along z
+                            const R bxW = pv<R, C>(Pm, PV_BH(0), pE), bxE = pv<R, C>(P0, PV_BH(0), pE);
+                            const R sxW = pv<R, C>(Pm, PV_FS(0, 1), pE), sxE = pv<R, C>(P0, PV_FS(0, 1), pE);
+                            const Corner<R> SW = corner<R, C>(Pm, pW, 1, R(1), R(1), bzS, szS, bxW, sxW);
+                            const Corner<R> SE = corner<R, C>(P0, pW, 1, R(-1), R(1), bzS, szS, bxE, sxE);
+                            const Corner<R> NW = corner<R, C>(Pm, pE, 1, R(1), R(-1), bzN, szN, bxW, sxW);
+                            const Corner<R> NE = corner<R, C>(P0, pE, 1, R(-1), R(-1), bzN, szN, bxE, sxE);
+                            Ey[j * (C::TX + 1) + i] = emf2d(SW, SE, NW, NE, gamma);
+                        }
                     }
                 }
             }
             __syncthreads();
-            // ---- a9: update plane u = c-1 (3D) or the single plane
-            const int u = C::AZ ? c - 1 : 0;
-            if ((C::AZ && c >= 1 && u < nz) || (!C::AZ)) {
-                const R* IB = S.I(C::AZ ? (u & 1) : 0);
-                const R* Fx = IB;
-                const R* Fy = IB + 5 * C::FXN;
-                const R* Ez = Fy + 5 * C::FYN;
-                const R* ZL = S.Z(C::AZ ? (u & 1) : 0);        // level u-1/2
-                const R* ZH = S.Z(C::AZ ? ((u + 1) & 1) : 0);  // level u+1/2
-                const R* FzL = ZL;
-                const R* FzH = ZH;
-                const R* ExL = ZL + 5 * C::FZN;
-                const R* ExH = ZH + 5 * C::FZN;
-                const R* EyL = ExL + C::EXN;
-                const R* EyH = ExH + C::EXN;
-                const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
-                for (int w = threadIdx.x; w < C::TX * C::TY; w += C::NT) {
-                    const int i = w % C::TX, j = w / C::TX;
-                    if (i >= wx || j >= wy) continue;
-                    const int x = x0 + i + pt.gx, y = C::AY ? y0 + j + pt.gy : 0, z = u + pt.gz;
-                    const int64_t o = pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
-                    R du[5];
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) {
-                        R d = dtdx0 * (Fx[v * C::FXN + j * (C::TX + 1) + i + 1] - Fx[v * C::FXN + j * (C::TX + 1) + i]);
-                        if (C::AY) d += dtdx1 * (Fy[v * C::FYN + (j + 1) * C::TX + i] - Fy[v * C::FYN + j * C::TX + i]);
-                        if (C::AZ) d += dtdx2 * (FzH[v * C::FZN + j * C::TX + i] - FzL[v * C::FZN + j * C::TX + i]);
-                        du[v] = -d;
-                    }
-                    const int ez = j * (C::TX + 1) + i;
-                    R dbx = R(0), dby, dbz;
-                    if (C::AY) dbx += dtdx1 * (Ez[ez + (C::TX + 1)] - Ez[ez]);
-                    if (C::AZ) dbx -= dtdx2 * (EyH[ez] - EyL[ez]);
-                    dby = -dtdx0 * (Ez[ez + 1] - Ez[ez]);
-                    if (C::AZ) dby += dtdx2 * (ExH[j * C::TX + i] - ExL[j * C::TX + i]);
-                    dbz = dtdx0 * (EyL[ez + 1] - EyL[ez]);
-                    if (C::AY) dbz -= dtdx1 * (ExL[(j + 1) * C::TX + i] - ExL[j * C::TX + i]);
-                    const R* Ub = a.U + o;
-                    R* Un = a.Unew + o;
-                    R nv[8];
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) nv[v] = Ub[v * vol] + du[v];
-                    nv[5] = Ub[5 * vol] + dbx;
-                    nv[6] = Ub[6 * vol] + dby;
-                    nv[7] = Ub[7 * vol] + dbz;
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) Un[v * vol] = nv[v];
-                    if (!(nv[0] > R(0)) || !isfinite((double)nv[4])) atomicOr(a.err, ERR_PHYS);
-                }
+            if (!C::AZ) {
+                stage_update<R, C>(S, a.U, a.Unew, pt, x0, y0, 0, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
             }
         }
         // next tile
