@@ -176,6 +176,36 @@ void mhd_bunch_destroy(mhd_bunch *b);
 /* Thread-local text of the last error returned by any call on this thread. */
 const char *mhd_last_error(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free CFL time step.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory through the CUDA runtime -- code
+ * running while its stream is captured into a CUDA graph, hosts whose framework hands
+ * out all device memory from its own pool, real-time loops that cannot afford an
+ * allocation.  It needs no handle and calls no cudaMalloc / cudaFree (nor any other
+ * allocating routine): its scratch is a static device array inside the library holding
+ * one partial maximum per patch, MHD_NOALLOC_MAX_PATCHES entries (128 KB of doubles plus
+ * a 4-byte counter), which every GPU that loads the library keeps until the process exits.
+ *
+ * Computes the same dt as mhd_bunch_cfl_dt (courant / max over interior cells of
+ * sum_d (|u_d| + c_f,d)/dx_d) for `npatch` equal patches of nx*ny*nz active cells stored
+ * back to back in the state layout above (patch p at element p*8*X*Y*Z, guard ghosts on
+ * active axes; ghost faces next to the interior must be filled).  Writes the double dt
+ * to dt_dev (device memory) on cuda_stream (NULL: legacy default stream) without
+ * synchronising.  real_bytes 4 or 8; npatch above MHD_NOALLOC_MAX_PATCHES is rejected
+ * with MHD_EINVAL before any device work.  Cells whose rate is not finite are skipped
+ * and not reported (the handle API reports them).
+ *
+ * Every call shares the one static array, which keeps the last call's contents (the
+ * counter that must start at zero is cleared on the stream before each launch): calls
+ * whose kernels may overlap on the GPU, e.g. on two streams at once, race and must be
+ * ordered by the caller.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before any stream
+ * capture begins. */
+#define MHD_NOALLOC_MAX_PATCHES 16384
+int mhd_cfl_dt_uniform_noalloc(const void *state, int real_bytes, int npatch, int nx, int ny,
+                               int nz, int guard, const double dx[3], double gamma,
+                               double courant, void *dt_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

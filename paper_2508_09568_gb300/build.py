@@ -20,6 +20,7 @@ UNITS = {
     "kernels_f32.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "kernels_f64.cu": [],
     "mhd_bunch.cu": [],
+    "mhd_noalloc.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

@@ -54,7 +54,9 @@ SIGNATURES = {
     "mhd_bunch_launch_count": (I, [P, I64P]),
     "mhd_bunch_destroy": (None, [P]),
     "mhd_last_error": (ct.c_char_p, []),
+    "mhd_cfl_dt_uniform_noalloc": (I, [P, I, I, I, I, I, I, DP, D, D, P, P]),
 }
+MHD_NOALLOC_MAX_PATCHES = 16384
 
 _LIB = None
 

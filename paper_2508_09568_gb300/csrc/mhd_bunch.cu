@@ -42,6 +42,11 @@ double hlld_eps(int rb) { return rb == 8 ? 1e-12 : 1e-6; }
 
 }  // namespace
 
+namespace mhd {
+// lets other translation units of the library report through mhd_last_error()
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace mhd
+
 struct mhd_bunch {
     int rb = 4, guard = 3, npatch = 0, ndim = 3;
     std::vector<int> pn;                 // 3 * npatch
