@@ -12,7 +12,7 @@ static const StepLaunch kStepF64[] = {
 
 const PrecisionKernels& kernels_f64() {
     static const PrecisionKernels k{kStepF64, (int)(sizeof(kStepF64) / sizeof(kStepF64[0])), &launch_fill<double>,
-                                    &launch_cfl<double>};
+                                    &launch_cfl<double>, &launch_adjoint<double>, AF_N};
     return k;
 }
 

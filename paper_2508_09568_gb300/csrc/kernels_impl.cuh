@@ -1,6 +1,7 @@
 // Instantiation helpers shared by the per-precision translation units.
 #pragma once
 
+#include "mhd_adjoint.cuh"
 #include "mhd_aux.cuh"
 #include "mhd_launch.h"
 #include "mhd_step.cuh"
@@ -76,6 +77,46 @@ static cudaError_t launch_cfl(const void* U, const PatchDev* patches, int npatch
     a.dt_out = dt_out;
     a.err = err;
     cfl_kernel<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsigned* err, cudaStream_t s,
+                                  int* nlaunch) {
+    AdjArgs<R> a;
+    a.U = static_cast<const R*>(h.U);
+    a.lam_next = static_cast<const R*>(h.lam_next);
+    a.lam = static_cast<R*>(h.lam);
+    a.F = static_cast<R*>(h.F);
+    a.G = static_cast<R*>(h.G);
+    a.ncell = h.ncell;
+    a.patches = h.patches;
+    a.npatch = h.npatch;
+    a.gamma = h.gamma;
+    a.eps = h.eps;
+    a.dt = h.dt;
+    for (int d = 0; d < 3; ++d) a.dxi[d] = h.dxi[d];
+    a.limiter = h.limiter;
+    const int bx = (h.max_cells + 255) / 256 < 64 ? (h.max_cells + 255) / 256 : 64;
+    const dim3 grid(bx, h.npatch < 65535 ? h.npatch : 65535), blk(256);
+    dim3 fgrid(8, h.npatch < 65535 ? h.npatch : 65535);
+    int n = 0;
+    fill_kernel<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.U), h.patches, h.npatch, fg, err); ++n;
+    adj_fwd_prim<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_fwd_slopes<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_fwd_en<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_fwd_bh<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_fwd_wh<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_init<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_faces<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_edges<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_pred<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_bh<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_en<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_slopes<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_prim<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_fill_transpose<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.lam), h.patches, h.npatch, fg, err); ++n;
+    if (nlaunch) *nlaunch = n;
     return cudaGetLastError();
 }
 

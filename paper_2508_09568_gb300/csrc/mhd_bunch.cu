@@ -80,6 +80,9 @@ struct mhd_bunch {
     double* d_dts = nullptr;             // dt per step of advance_host
     int d_dts_cap = 0;
     unsigned* d_err = nullptr;
+    void* d_adjF = nullptr;              // adjoint work arrays (allocated on first use)
+    void* d_adjG = nullptr;
+    void* d_adjU = nullptr;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;                         // index of the buffer holding U^n
     cudaStream_t stream = nullptr;
@@ -750,6 +753,9 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     cudaFree(b->d_dt);
     cudaFree(b->d_dts);
     cudaFree(b->d_err);
+    cudaFree(b->d_adjF);
+    cudaFree(b->d_adjG);
+    cudaFree(b->d_adjU);
     delete b;
 }
 
@@ -758,10 +764,48 @@ const char* mhd_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 
 extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, const void* lam_next, void* lam) {
-    (void)dt;
-    (void)U_n;
-    (void)lam_next;
-    (void)lam;
-    if (!b) return fail(MHD_EINVAL, "handle is NULL");
-    return fail(MHD_ESTATE, "adjoint kernels not built in this version");
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!U_n || !lam_next || !lam) return fail(MHD_EINVAL, "NULL argument");
+    if (!(dt >= 0) || !std::isfinite(dt)) return fail(MHD_EINVAL, "dt must be finite and >= 0");
+    if (b->ndim != 3) return fail(MHD_EINVAL, "the adjoint is implemented for 3D bunches");
+    if (lam == lam_next || lam == U_n) return fail(MHD_EINVAL, "lam must not alias U_n or lam_next");
+    const int64_t ncell = (int64_t)(b->state_bytes / b->rb) / 8;
+    const size_t fbytes = (size_t)b->K->adj_fields * (size_t)ncell * b->rb;
+    if (!b->d_adjF) {
+        // library-owned work arrays, kept for later calls (released by mhd_bunch_destroy)
+        cudaError_t e = cudaMalloc(&b->d_adjF, fbytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_adjG, fbytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_adjU, b->state_bytes);
+        if (e != cudaSuccess) {
+            cudaFree(b->d_adjF);
+            cudaFree(b->d_adjG);
+            cudaFree(b->d_adjU);
+            b->d_adjF = b->d_adjG = b->d_adjU = nullptr;
+            return fail(MHD_ENOMEM, std::string("adjoint work arrays: ") + cudaGetErrorString(e));
+        }
+    }
+    CK(cudaMemcpyAsync(b->d_adjU, U_n, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream));
+    CK(cudaMemsetAsync(b->d_adjG, 0, fbytes, b->stream));
+    AdjHostArgs a;
+    a.U = b->d_adjU;
+    a.lam_next = lam_next;
+    a.lam = lam;
+    a.F = b->d_adjF;
+    a.G = b->d_adjG;
+    a.ncell = ncell;
+    a.patches = b->d_patches;
+    a.npatch = b->npatch;
+    int mc = 0;
+    for (const auto& q : b->hp) mc = std::max(mc, q.X * q.Y * q.Z);
+    a.max_cells = mc;
+    a.gamma = b->gamma;
+    a.eps = hlld_eps(b->rb);
+    a.dt = dt;
+    for (int d = 0; d < 3; ++d) a.dxi[d] = 1.0 / b->dx[d];
+    a.limiter = b->limiter;
+    int n = 0;
+    CK(b->K->adjoint(a, b->fg, b->d_err, b->stream, &n));
+    b->launches += n;
+    return MHD_OK;
 }

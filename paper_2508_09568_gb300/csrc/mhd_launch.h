@@ -17,6 +17,22 @@ struct StepLaunch {
     cudaError_t (*launch)(const void* args, int grid, cudaStream_t s);
 };
 
+// arguments of the adjoint step (see mhd_adjoint.cuh), precision independent
+struct AdjHostArgs {
+    void* U;             // scratch copy of U^n (ghosts filled here)
+    const void* lam_next;
+    void* lam;
+    void* F;             // forward work fields
+    void* G;             // cotangent work fields
+    int64_t ncell;
+    const PatchDev* patches;
+    int npatch;
+    int max_cells;       // largest padded patch
+    double gamma, eps, dt;
+    double dxi[3];
+    int limiter;
+};
+
 // Kernel entry points of one precision (R = float or double).
 struct PrecisionKernels {
     const StepLaunch* step;
@@ -27,6 +43,10 @@ struct PrecisionKernels {
     cudaError_t (*cfl)(const void* U, const PatchDev* patches, int npatch, double gamma, double courant,
                        const double dxi[3], const int act[3], void* partial, int grid, unsigned* counter,
                        double* dt_out, unsigned* err, cudaStream_t s);
+    // the whole adjoint kernel sequence (fill of the U copy, forward recompute, reverse);
+    // G must be zeroed before the call
+    cudaError_t (*adjoint)(const AdjHostArgs& a, const FillGeom& fg, unsigned* err, cudaStream_t s, int* nlaunch);
+    int adj_fields;      // work fields per cell in F and in G
 };
 
 const PrecisionKernels& kernels_f32();

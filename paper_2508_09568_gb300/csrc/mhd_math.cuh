@@ -12,6 +12,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef MHD_HD
+#define MHD_HD __host__ __device__ __forceinline__
+#endif
+
 namespace mhd {
 
 // Variable order of the state and of the primitive vector.
@@ -20,26 +24,22 @@ enum { V_RHO = 0, V_MX = 1, V_MY = 2, V_MZ = 3, V_EN = 4, V_BX = 5, V_BY = 6, V_
 enum { Q_RHO = 0, Q_U = 1, Q_V = 2, Q_W = 3, Q_P = 4, Q_BX = 5, Q_BY = 6, Q_BZ = 7 };
 
 template <typename R>
-__device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+MHD_HD R rabs(R x) { return x < R(0) ? -x : x; }
 
-template <typename R>
-__device__ __forceinline__ R rsqrt_(R x);
-template <>
-__device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
-template <>
-__device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+MHD_HD float rsqrt_(float x) { return sqrtf(x); }
+MHD_HD double rsqrt_(double x) { return sqrt(x); }
 
 // max/min with ties going to the first argument (the subgradient choice of the adjoint)
 template <typename R>
-__device__ __forceinline__ R fmax1(R a, R b) { return a >= b ? a : b; }
+MHD_HD R fmax1(R a, R b) { return a >= b ? a : b; }
 template <typename R>
-__device__ __forceinline__ R fmin1(R a, R b) { return a <= b ? a : b; }
+MHD_HD R fmin1(R a, R b) { return a <= b ? a : b; }
 
 // Limited undivided slope from the two one-sided differences a = q_i - q_{i-1},
 // b = q_{i+1} - q_i (Sec. 2.1.4).  limiter 0: minmod, 1: monotonised central.
 // Zero when a*b <= 0; otherwise the selected candidate (ties: the first).
 template <typename R>
-__device__ __forceinline__ R limited(R a, R b, int limiter) {
+MHD_HD R limited(R a, R b, int limiter) {
     R pick;
     if (limiter == 0) {
         pick = rabs(a) <= rabs(b) ? a : b;
@@ -55,7 +55,7 @@ __device__ __forceinline__ R limited(R a, R b, int limiter) {
 // cf^2 = 1/2 (cs^2 + ca^2 + sqrt(disc)), disc = (cs^2 + ca^2)^2 - 4 cs^2 can^2 evaluated
 // as (cs^2 - can^2)^2 + cat^2 (2 (cs^2 + can^2) + cat^2) (identical, no cancellation).
 template <typename R>
-__device__ __forceinline__ R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
+MHD_HD R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
     R cs2 = gP * rho_inv;
     R can2 = bn * bn * rho_inv;
     R cat2 = (bt1 * bt1 + bt2 * bt2) * rho_inv;
@@ -67,7 +67,7 @@ __device__ __forceinline__ R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
 // Primitive state from the conserved one; the cell-centred field is the mean of the two
 // faces of the cell (Sec. 2.1 EOS: P = (gamma-1)(E - rho u^2/2 - B^2/2)).
 template <typename R>
-__device__ __forceinline__ void cons_to_prim(R rho, R mx, R my, R mz, R E, R bxc, R byc, R bzc,
+MHD_HD void cons_to_prim(R rho, R mx, R my, R mz, R E, R bxc, R byc, R bzc,
                                              R gm1, R q[8]) {
     R ri = R(1) / rho;
     R u = mx * ri, v = my * ri, w = mz * ri;
@@ -87,7 +87,7 @@ __device__ __forceinline__ void cons_to_prim(R rho, R mx, R my, R mz, R E, R bxc
 // field components of the result are set by the caller from the predicted faces.
 // D[d][k]: slope of primitive k along d divided by dx_d (zero on collapsed axes).
 template <typename R>
-__device__ __forceinline__ void hancock(const R q[8], const R D[3][8], R hdt, R gamma, R out[5]) {
+MHD_HD void hancock(const R q[8], const R D[3][8], R hdt, R gamma, R out[5]) {
     const R u = q[Q_U], v = q[Q_V], w = q[Q_W], rho = q[Q_RHO], P = q[Q_P];
     const R divu = D[0][Q_U] + D[1][Q_V] + D[2][Q_W];
     const R ri = R(1) / rho;
@@ -112,7 +112,7 @@ __device__ __forceinline__ void hancock(const R q[8], const R D[3][8], R hdt, R 
 // the star state is degenerate when |D| <= eps*bn^2 (then transverse v, B keep their
 // outer values); ties at x/t = 0 take the left state.
 template <typename R>
-__device__ __forceinline__ void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps,
+MHD_HD void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps,
                                      R F[5]) {
     const R bn2 = bn * bn;
     // outer states
@@ -224,7 +224,7 @@ struct Corner {
 // S_E = max(0, max ua+cf_a), S_W = min(0, min ua-cf_a), S_N, S_S likewise along b.
 // It reduces to the 1D HLL induction flux when the states do not vary along a or b.
 template <typename R>
-__device__ __forceinline__ R emf2d(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>& NW,
+MHD_HD R emf2d(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>& NW,
                                    const Corner<R>& NE, R gamma) {
     R ap[4], am[4], bp[4], bm[4];
     const Corner<R>* st[4] = {&SW, &SE, &NW, &NE};

@@ -1,0 +1,338 @@
+"""GPU adjoint of the bunch step against the oracle's reference gradient and finite differences.
+
+* one step, FP64: lam from mhd_bunch_step_adjoint equals the gradient torch autograd takes
+  through the FP64 oracle (guard fill included), to 1e-10 (max-norm relative);
+* one step, FP32 adjoint against the same FP64 reference on the FP32-rounded state;
+* dot-product test of the adjoint against central finite differences of the GPU forward;
+* the checkpointed rollout (torch.autograd.Function) against central finite differences,
+  on the adjoint workload: 64^3 box of 8 patches of 32^3, 200 fixed-dt steps, loss
+  sum((rho_T - rho_target)^2), gradient with respect to the initial velocity.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mhd as O
+from paper_2508_09568_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def interior_mask(geom):
+    m = np.zeros(geom.state_elems(), dtype=bool)
+    ones = np.ones((8,) + tuple(int(v) for v in geom.domain[::-1]))
+    idx = W.to_patches(ones, geom)
+    m[:] = np.isfinite(idx)
+    return m
+
+
+def oracle_grad(geom, flat, dt, gamma, w, limiter=0, eps=O.HLLD_EPS[8]):
+    """d/dU0 of sum(w * U1) through fill + step of the FP64 oracle (torch autograd)."""
+    U0 = torch.tensor(flat, dtype=torch.float64, requires_grad=True)
+    offs = geom.offsets()
+    patches = []
+    for p in range(geom.npatch):
+        Z, Y, X = geom.padded(p)
+        patches.append(U0[offs[p]: offs[p] + 8 * X * Y * Z].reshape(8, Z, Y, X))
+    filled = O.fill_guards(patches, geom)
+    out = O.step(torch.stack(filled), dt, geom.active, geom.dx, gamma, limiter, eps, gvec=geom.gvec,
+                 n=geom.patch_n[0])
+    U1 = torch.cat([o.reshape(-1) for o in out])
+    (torch.tensor(w) * U1).sum().backward()
+    return U0.grad.numpy()
+
+
+def gpu_adjoint(geom, flat, dt, gamma, w, dtype, limiter=0):
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    b = MHDBunch(geom, dtype=dtype, gamma=gamma, limiter=limiter)
+    U = torch.tensor(flat, dtype=dtype, device="cuda")
+    lam_next = torch.tensor(w, dtype=dtype, device="cuda")
+    lam = torch.full_like(U, float("nan"))
+    with torch.cuda.stream(b.stream):
+        b.step_adjoint(dt, U, lam_next, lam)
+    b.stream.synchronize()
+    code, msg = b.error()
+    assert code == 0, msg
+    return lam.double().cpu().numpy(), b
+
+
+def setup(seed, ncell=(16, 16, 16), patch=(8, 8, 8)):
+    geom, U, meta = W.small_box(ncell=ncell, patch=patch, seed=seed)
+    flat = W.to_patches(U, geom)
+    ob = O.Bunch(geom, meta["gamma"])
+    dt = ob.cfl_dt(ob.fill_guards(ob.split(flat)))
+    mask = interior_mask(geom)
+    rng = np.random.default_rng(seed + 100)
+    w = np.where(mask, rng.normal(size=flat.size), 0.0)
+    return geom, flat, meta["gamma"], dt, w, mask
+
+
+@pytest.mark.parametrize("limiter", [0, 1], ids=["minmod", "mc"])
+def test_adjoint_matches_oracle_autograd_fp64(limiter):
+    geom, flat, gamma, dt, w, mask = setup(41)
+    ref = oracle_grad(geom, flat, dt, gamma, w, limiter)
+    got, _ = gpu_adjoint(geom, flat, dt, gamma, w, torch.float64, limiter)
+    assert np.all(got[~mask] == 0.0)
+    err = np.max(np.abs(got[mask] - ref[mask])) / np.max(np.abs(ref[mask]))
+    assert err <= 1e-10, err
+
+
+def test_adjoint_ragged_tiles_and_several_patch_shapes_fp64():
+    geom, flat, gamma, dt, w, mask = setup(42, ncell=(24, 16, 20), patch=(12, 16, 10))
+    ref = oracle_grad(geom, flat, dt, gamma, w)
+    got, _ = gpu_adjoint(geom, flat, dt, gamma, w, torch.float64)
+    err = np.max(np.abs(got[mask] - ref[mask])) / np.max(np.abs(ref[mask]))
+    assert err <= 1e-10, err
+
+
+def test_adjoint_fp32_against_fp64_reference():
+    geom, flat, gamma, dt, w, mask = setup(43)
+    flat32 = flat.astype(np.float32).astype(np.float64)
+    ref = oracle_grad(geom, flat32, dt, gamma, w, eps=O.HLLD_EPS[4])
+    got, _ = gpu_adjoint(geom, flat32, dt, gamma, w, torch.float32)
+    err = np.max(np.abs(got[mask] - ref[mask])) / np.max(np.abs(ref[mask]))
+    assert err <= 1e-4, err
+
+
+def jitter(flat, mask, seed, amp=1e-2):
+    """Seeded relative plus absolute noise on every interior entry: a generic state with no
+    exactly tied or exactly zero one-sided differences (a field that is identically zero, like
+    B_z of the adjoint workload, stays zero under relative noise alone), where the step is
+    differentiable; at exact ties the limiter sits on its kink and central differences
+    measure a one-sided slope instead of the adjoint's subgradient."""
+    rng = np.random.default_rng(seed)
+    n1 = rng.uniform(-1, 1, size=flat.size)
+    n2 = rng.uniform(-1, 1, size=flat.size)
+    return np.where(mask, flat * (1.0 + amp * n1) + 0.1 * amp * n2, flat)
+
+
+def test_adjoint_dot_product_finite_differences_fp64():
+    geom, flat, gamma, dt, w, mask = setup(44)
+    flat = jitter(flat, mask, 440)
+    lam, b = gpu_adjoint(geom, flat, dt, gamma, w, torch.float64)
+    rng = np.random.default_rng(7)
+
+    def fwd(x):
+        b.upload(x)
+        b.fill_guards()
+        b.step(dt)
+        return b.download()
+
+    for _ in range(3):
+        d = np.where(mask, rng.normal(size=flat.size), 0.0)
+        h = 1e-8   # the step is piecewise smooth (limiter, wave-speed and Riemann-region
+        #            switches); h must stay well below the distance to the nearest switch
+        jd = (fwd(flat + h * d) - fwd(flat - h * d)) / (2 * h)
+        lhs = float(np.sum(w[mask] * jd[mask]))
+        rhs = float(np.sum(lam[mask] * d[mask]))
+        assert abs(lhs - rhs) <= 1e-6 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def _oracle_rollout_grad(geom, flat, dt, gamma, steps, wmask, target):
+    """d/dU0 of sum over wmask of (U_T - target)^2 through `steps` oracle steps (autograd)."""
+    U = torch.tensor(flat, dtype=torch.float64, requires_grad=True)
+    cur = U
+    offs = geom.offsets()
+    for _ in range(steps):
+        patches = []
+        for p in range(geom.npatch):
+            Z, Y, X = geom.padded(p)
+            patches.append(cur[offs[p]: offs[p] + 8 * X * Y * Z].reshape(8, Z, Y, X))
+        filled = O.fill_guards(patches, geom)
+        out = O.step(torch.stack(filled), dt, geom.active, geom.dx, gamma, gvec=geom.gvec, n=geom.patch_n[0])
+        cur = torch.cat([o.reshape(-1) for o in out])
+    m = torch.tensor(wmask)
+    L = torch.sum(torch.where(m, (cur - torch.tensor(target)) ** 2, torch.zeros((), dtype=cur.dtype)))
+    L.backward()
+    return U.grad.numpy(), float(L)
+
+
+def test_rollout_matches_oracle_autograd_and_step_chain():
+    """A 12-step checkpointed rollout (checkpoint every 5) on a 16^3 box of 8^3 patches: the
+    gradient of a density misfit equals torch autograd through 12 oracle steps (the naive FP64
+    torch-op reference) and the chain of single MHDStep applications."""
+    from paper_2508_09568_gb300.autograd import MHDStep, rollout
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, flat, gamma, dt, w, mask = setup(45)
+    flat = jitter(flat, mask, 4500)   # a generic point (this seed's pressure has exact ties)
+    dt = 0.4 * dt      # a fixed dt well inside the stability limit for the whole run
+    steps = 12
+    rng = np.random.default_rng(450)
+    target = np.where(mask, flat * (1.0 + 1e-3 * rng.normal(size=flat.size)), 0.0)
+    offs = geom.offsets()
+    vol = int(np.prod(geom.padded(0)))
+    dmask = np.zeros(flat.size, dtype=bool)
+    for q in range(geom.npatch):
+        dmask[offs[q]: offs[q] + vol] = mask[offs[q]: offs[q] + vol]
+    ref, Lref = _oracle_rollout_grad(geom, flat, dt, gamma, steps, dmask, target)
+    bunch = MHDBunch(geom, dtype=torch.float64, gamma=gamma)
+    tgt = torch.tensor(target, device="cuda")
+    dm = torch.tensor(dmask, device="cuda")
+    grads = []
+    for mode in ("rollout", "chain"):
+        U0 = torch.tensor(flat, device="cuda", requires_grad=True)
+        if mode == "rollout":
+            UT = rollout(U0, bunch, dt, steps, 5)
+        else:
+            UT = U0
+            for _ in range(steps):
+                UT = MHDStep.apply(UT, bunch, dt)
+        L = torch.sum(torch.where(dm, (UT - tgt) ** 2, torch.zeros((), dtype=UT.dtype, device="cuda")))
+        L.backward()
+        assert abs(float(L.detach()) - Lref) <= 1e-10 * Lref
+        grads.append(U0.grad.detach().cpu().numpy())
+    for g in grads:
+        err = np.max(np.abs(g[mask] - ref[mask])) / np.max(np.abs(ref[mask]))
+        assert err <= 1e-10, err
+
+
+def _global_to_patch_index(geom):
+    N = geom.domain
+    ids = np.arange(8 * N[0] * N[1] * N[2], dtype=np.float64).reshape(8, N[2], N[1], N[0])
+    idx = W.to_patches(ids, geom)
+    ok = np.isfinite(idx)
+    return torch.tensor(np.where(ok, idx, 0).astype(np.int64)), torch.tensor(ok)
+
+
+def _workload(dev="cuda"):
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, make_state, v0, vt, meta = W.adjoint_box()
+    gamma = meta["gamma"]
+    gi, ok = _global_to_patch_index(geom)
+    gi, ok = gi.to(dev), ok.to(dev)
+    rho = torch.tensor(meta["rho"], device=dev)
+    p = torch.tensor(meta["p"], device=dev)
+    b = [torch.tensor(x, device=dev) for x in meta["b"]]
+
+    def state_of(v):
+        # the set-up's own map v -> U0 (rho, p, face B fixed); B is uniform so B_c = B_face
+        m = [rho * v[d] for d in range(3)]
+        E = p / (gamma - 1) + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2) + 0.5 * (b[0] ** 2 + b[1] ** 2 + b[2] ** 2)
+        G = torch.stack([rho, m[0], m[1], m[2], E, b[0], b[1], b[2]]).reshape(-1)
+        return torch.where(ok, G[gi], torch.zeros((), dtype=G.dtype, device=dev))
+
+    bunch = MHDBunch(geom, dtype=torch.float64, gamma=gamma)
+    bunch.upload(W.to_patches(make_state(v0), geom))
+    bunch.fill_guards()
+    dt = 0.5 * bunch.cfl_dt()   # Courant 0.4 (the default is 0.8): fixed, not differentiated
+    offs = geom.offsets()
+    vol = int(np.prod(geom.padded(0)))
+    im = interior_mask(geom)
+    dmask = np.zeros(geom.state_elems(), dtype=bool)
+    for q in range(geom.npatch):     # interior density entries (variable 0 of each patch)
+        dmask[offs[q]: offs[q] + vol] = im[offs[q]: offs[q] + vol]
+    return geom, state_of, v0, vt, meta, bunch, dt, torch.tensor(dmask, device=dev)
+
+
+def test_adjoint_matches_oracle_on_adjoint_workload_one_step():
+    """One step of the 64^3 adjoint workload (8 patches of 32^3), at its initial state with 1e-2
+    seeded relative noise: the GPU adjoint equals torch autograd through the FP64 oracle
+    (guard fill included).  The noise matters: the workload's pressure is uniform up to
+    rounding, so without it the limiter's arguments tie at rounding level and the GPU and
+    the oracle, whose roundings differ, pick different (equally valid) subgradients."""
+    geom, make_state, v0, vt, meta = W.adjoint_box()
+    flat = W.to_patches(make_state(v0), geom)
+    mask = interior_mask(geom)
+    flat = jitter(flat, mask, 600)
+    ob = O.Bunch(geom, meta["gamma"])
+    dt = 0.5 * ob.cfl_dt(ob.fill_guards(ob.split(flat)))
+    rng = np.random.default_rng(60)
+    w = np.where(mask, rng.normal(size=flat.size), 0.0)
+    ref = oracle_grad(geom, flat, dt, meta["gamma"], w)
+    got, _ = gpu_adjoint(geom, flat, dt, meta["gamma"], w, torch.float64)
+    err = np.max(np.abs(got[mask] - ref[mask])) / np.max(np.abs(ref[mask]))
+    assert err <= 1e-10, err
+
+
+def test_rollout_gradient_of_adjoint_workload():
+    """64^3 = 8 x 32^3, 200 fixed-dt steps, checkpoint every 10, loss sum((rho_T - rho_target)^2),
+    gradient with respect to the initial velocity:
+      * the checkpointed rollout equals the chain of 200 single steps without checkpoints;
+      * central differences of the full 200-step loss agree within 2e-3.  The limiter and
+        the HLLD wave-speed estimates (min/max of the face states, nearly equal in smooth
+        flow) make the loss piecewise smooth with densely packed switches, so differences
+        of the long rollout converge only like O(h) (measured 4e-4 at h = 1e-8); the
+        1e-6 agreement is checked on a short horizon in the next test."""
+    from paper_2508_09568_gb300.autograd import MHDStep, rollout
+    geom, state_of, v0, vt, meta, bunch, dt, dmask = _workload()
+    steps, ck = meta["steps"], meta["ckpt"]
+    zero = torch.zeros((), dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        target = rollout(state_of(torch.tensor(vt, device="cuda")), bunch, dt, steps, ck)
+
+    def loss_of(v, chain=False):
+        if chain:
+            UT = state_of(v)
+            for _ in range(steps):
+                UT = MHDStep.apply(UT, bunch, dt)
+        else:
+            UT = rollout(state_of(v), bunch, dt, steps, ck)
+        return torch.sum(torch.where(dmask, (UT - target) ** 2, zero))
+
+    grads = []
+    for chain in (False, True):
+        v = torch.tensor(v0, device="cuda", requires_grad=True)
+        L = loss_of(v, chain)
+        L.backward()
+        grads.append(v.grad.detach())
+    g = grads[0]
+    assert torch.isfinite(g).all()
+    assert float(torch.max(torch.abs(grads[1] - g)) / torch.max(torch.abs(g))) <= 1e-10
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        d = torch.tensor(rng.normal(size=v0.shape), device="cuda")
+        h = 1e-8
+        with torch.no_grad():
+            fd = (loss_of(torch.tensor(v0, device="cuda") + h * d) - loss_of(torch.tensor(v0, device="cuda") - h * d)) / (2 * h)
+        an = torch.sum(g * d)
+        assert abs(float(fd - an)) <= 2e-3 * abs(float(an)), (float(fd), float(an))
+
+
+def test_rollout_gradient_short_horizon_fd_1e6():
+    """Two checkpointed steps of the adjoint workload from its initial state with seeded noise
+    on every interior entry (a point where the step is differentiable with margin: no exactly
+    tied limiter or wave-speed arguments); the density misfit is taken against a run from a
+    nearby state so that the loss is small and its differences keep their precision.  The
+    gradient with respect to the initial state agrees with central differences (h = 1e-8)
+    to 1e-6, along 16 single components (the largest gradient entries) and 2 random
+    directions."""
+    from paper_2508_09568_gb300.autograd import rollout
+    geom, state_of, v0, vt, meta, bunch, dt, dmask = _workload()
+    m = interior_mask(geom)
+    mask = torch.tensor(m, device="cuda")
+    rng = np.random.default_rng(11)
+    with torch.no_grad():
+        base = state_of(torch.tensor(v0, device="cuda")).cpu().numpy()
+        U0 = torch.tensor(jitter(base, m, 11), device="cuda")
+        Ut = torch.tensor(jitter(U0.cpu().numpy(), m, 12, amp=1e-4), device="cuda")
+        target = rollout(Ut, bunch, dt, 2, 1)
+    zero = torch.zeros((), dtype=torch.float64, device="cuda")
+
+    def loss_of(U):
+        UT = rollout(U, bunch, dt, 2, 1)
+        return torch.sum(torch.where(dmask, (UT - target) ** 2, zero))
+
+    U = U0.clone().requires_grad_(True)
+    loss_of(U).backward()
+    g = U.grad.detach()
+    dirs = []
+    for e in torch.argsort(torch.abs(g), descending=True)[:16].tolist():
+        d = torch.zeros_like(U0)
+        d[e] = 1.0
+        dirs.append(d)
+    for _ in range(2):
+        dirs.append(torch.where(mask, torch.tensor(rng.normal(size=U0.numel()), device="cuda"), zero))
+    h = 1e-8
+    used = 0
+    for d in dirs:
+        with torch.no_grad():
+            fd1 = float((loss_of(U0 + h * d) - loss_of(U0 - h * d)) / (2 * h))
+            fd2 = float((loss_of(U0 + 2 * h * d) - loss_of(U0 - 2 * h * d)) / (4 * h))
+        an = float(torch.sum(g * d))
+        # a difference quotient is evidence only where the loss is smooth on [-2h, 2h]:
+        # there the two step sizes agree; a switch inside the interval breaks that
+        if abs(fd1 - fd2) > 2e-7 * abs(fd1):
+            continue
+        used += 1
+        assert abs(fd1 - an) <= 1e-6 * abs(an), (fd1, an)
+    assert used >= 14, used
