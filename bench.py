@@ -149,6 +149,100 @@ def cpu_baseline(steps=1):
                       f"guard fill + step, {el:.2f} s"}
 
 
+def _time_ms(stream, fn, n):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def ragged_leg(dev, steps):
+    """The ragged box: 1566 patches of 16^3 / 24^3 / 32^3 (24.55 M cells), FP32, one persistent
+    launch per step in a CUDA graph (autotuned tile); beside it the one-launch-per-patch path."""
+    from paper_2508_09568_gb300 import capi
+    from paper_2508_09568_gb300 import workloads as W
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, fields, meta = W.ragged_box()
+    flat = W.to_patches(fields, geom, dtype=np.float32)
+    b = MHDBunch(geom, dtype=torch.float32, gamma=meta["gamma"], device=str(dev))
+    b.upload(flat)
+    b.set_mode(capi.MHD_MODE_PERSISTENT, -1)
+    cfg = b.autotune(None)
+    dts = torch.zeros(1, dtype=torch.float64, device=dev)
+    b.graph_capture(1, dts)
+    for _ in range(3):
+        b.graph_launch()
+    ms = _time_ms(b.stream, b.graph_launch, steps)
+    cells = geom.interior_cells()
+    b.set_mode(capi.MHD_MODE_PER_PATCH, cfg)
+    dt_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def plain():
+        b.fill_guards()
+        b.cfl_dt_device(dt_dev)
+        b.step_device_dt(dt_dev)
+
+    plain()
+    ms_plain = _time_ms(b.stream, plain, 2)
+    code, msg = b.error()
+    b.close()
+    if code != 0:
+        raise RuntimeError(msg)
+    return {"workload": "ragged periodic box 288x288x296, 1566 patches of 16^3/24^3/32^3, OT fields, FP32",
+            "cells": cells, "value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "config_index": cfg,
+            "plain_per_patch": {"value": cells / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                                "launches_per_step": geom.npatch + 2}}
+
+
+def adjoint_leg(dev, dtype, rollout_steps=200, ckpt=10, reps=5):
+    """Adjoint / forward time on the adjoint workload (64^3 = 8 x 32^3, fixed dt): one step
+    (fill + update) against one adjoint step, and a checkpointed rollout's backward against
+    its forward."""
+    from paper_2508_09568_gb300 import workloads as W
+    from paper_2508_09568_gb300.autograd import rollout
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, make_state, v0, vt, meta = W.adjoint_box()
+    flat = W.to_patches(make_state(v0), geom)
+    b = MHDBunch(geom, dtype=dtype, gamma=meta["gamma"], device=str(dev))
+    b.upload(flat)
+    b.fill_guards()
+    dt = 0.5 * b.cfl_dt()
+    U = b.current().clone()
+    lam_next = torch.randn_like(U)
+    lam = torch.empty_like(U)
+
+    def fwd():
+        b.fill_guards()
+        b.step(dt)
+
+    def adj():
+        b.step_adjoint(dt, U, lam_next, lam)
+
+    with torch.cuda.stream(b.stream):
+        fwd()
+        adj()
+    t_f = _time_ms(b.stream, fwd, reps)
+    t_a = _time_ms(b.stream, adj, reps)
+    # checkpointed rollout (the autograd path)
+    U0 = U.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    UT = rollout(U0, b, dt, rollout_steps, ckpt)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    UT.backward(torch.randn_like(UT))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    b.close()
+    return {"forward_ms": t_f, "adjoint_ms": t_a, "ratio": t_a / t_f,
+            "rollout": {"steps": rollout_steps, "ckpt": ckpt, "forward_s": t1 - t0, "backward_s": t2 - t1,
+                        "ratio": (t2 - t1) / (t1 - t0)}}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -306,6 +400,11 @@ def run_ours(args, ws, rank, local):
            "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2},
            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "setup_s": {"generate": t_gen}}
+    if rank == 0 and not args.no_extra:
+        out["ragged"] = ragged_leg(dev, max(3, min(args.steps, 10)))
+        out["adjoint_forward_ratio"] = {"workload": "64^3 periodic box, 8 patches of 32^3, fixed dt",
+                                        "f64": adjoint_leg(dev, torch.float64),
+                                        "f32": adjoint_leg(dev, torch.float32)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(8)
     b.close()
@@ -326,6 +425,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-launch-per-patch comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--config", type=int, default=-1, help="tile configuration (default: autotune)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ragged-box and adjoint legs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

@@ -465,3 +465,27 @@ def small_box(ncell=(16, 16, 16), patch=(8, 8, 8), seed=7, gamma=5.0 / 3.0, amp=
     bz = fwd(Ay, 2) / dxv[0] - fwd(Ax, 1) / dxv[1]
     U = conserved_from_setup(rho, vel, p, (bx, by, bz), gamma)
     return geom, U, dict(gamma=gamma)
+
+
+def ragged_small(seed=5, gamma=5.0 / 3.0):
+    """A small periodic 48 x 48 x 36 box tiled by z-layers of 8^3, 12^3 and 16^3 patches (in
+    a seeded layer and patch order) with smooth seeded fields: the ragged layout of the
+    mixed-size box at a size the oracle follows in seconds."""
+    rng = np.random.default_rng(seed)
+    layers = [8, 12, 16]
+    layers = [layers[i] for i in rng.permutation(3)]
+    nxy = 48
+    sizes, origins = [], []
+    z0 = 0
+    for s in layers:
+        for j in range(nxy // s):
+            for i in range(nxy // s):
+                sizes.append([s, s, s])
+                origins.append([i * s, j * s, z0])
+        z0 += s
+    perm = rng.permutation(len(sizes))
+    sizes, origins = np.array(sizes)[perm], np.array(origins)[perm]
+    dx = 1.0 / nxy
+    geom = Geometry(sizes, origins, [nxy, nxy, z0], [dx, dx, dx], [[BC_PERIODIC] * 2] * 3, 3)
+    g2, U, meta = small_box(ncell=(nxy, nxy, z0), patch=(nxy, nxy, z0), seed=seed + 1000, gamma=gamma)
+    return geom, U, dict(gamma=gamma)
