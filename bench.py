@@ -36,6 +36,12 @@ UNIT = "cell-updates/s"
 FLOPS_PER_CELL = 3255.0
 BYTES_PER_CELL = {4: 64.0, 8: 128.0}       # read 8 values + write 8 values per cell-update
 SMS, FP32_LANES = 152, 128                 # GB300: SMs, FP32 lanes per SM
+# DRAM bytes (read + write) per cell-update of the fused step kernel, FP32, 32^3 patches,
+# 16 x 16 tiles of 512 threads: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture of a 192^3 box of the same patches and tiles (453.07 MB + 238.05 MB for
+# 7,077,888 cells).  Traffic scales with the number of patches, so a launch on the full
+# box moves this many bytes per cell.  Valid for this kernel version only.
+STEP_DRAM_BYTES_PER_CELL = {(4, 32, (16, 16, 512)): 691.12e6 / 7077888}
 
 
 def peaks():
@@ -268,7 +274,7 @@ def run_reference(args, ws, rank):
 def run_ours(args, ws, rank, local):
     from paper_2508_09568_gb300 import capi
     from paper_2508_09568_gb300 import workloads as W
-    from paper_2508_09568_gb300.bunch import MHDBunch
+    from paper_2508_09568_gb300.bunch import MHDBunch, fma_rate
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -372,15 +378,23 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": b.nbytes,
                "d2h_bytes_per_step": b.nbytes}
 
-    # ---- roofline of the dominant kernel (the fused step)
+    # ---- roofline of the dominant kernel (the fused step): SIMT-arithmetic bound; the
+    # peak is the FMA rate the library's probe kernel measures on this GPU
     step_s = t_step * 1e-3
-    alu_peak = SMS * FP32_LANES * 2 * sm_max_mhz * 1e6 / 1e12 if rb == 4 else None
+    alu_peak = fma_rate(dtype, str(dev)) / 1e12
+    derived = SMS * FP32_LANES * 2 * sm_max_mhz * 1e6 / 1e12 if rb == 4 else None
     flops = FLOPS_PER_CELL * cells / step_s / 1e12
     hbm = BYTES_PER_CELL[rb] * cells / step_s / 1e9
+    tpc = STEP_DRAM_BYTES_PER_CELL.get((rb, args.patch, tuple(tile)))
     roof = {"bound": "alu", "achieved": flops, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": (flops / alu_peak) if alu_peak else None, "traffic": None,
-            "kernel": "step_kernel", "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
-            "flops_per_cell": FLOPS_PER_CELL}
+            "frac": flops / alu_peak, "traffic": tpc * cells if tpc else None,
+            "kernel": "step_kernel",
+            "peak_source": f"measured: FMA-chain probe (mhd_probe_fma_rate), {args.dtype}",
+            "derived_peak": derived,
+            "derived_peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max_mhz:.0f} MHz",
+            "flops_per_cell": FLOPS_PER_CELL,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of a 192^3 "
+                              "capture, times the cells of one launch" if tpc else None}
     hbm_roof = {"bound": "hbm", "achieved": hbm, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm / hbm_gbs,
                 "bytes_per_cell": BYTES_PER_CELL[rb], "peak_source": peak_src,
                 "frac_of_whole_step": (BYTES_PER_CELL[rb] * value / ws / 1e9) / hbm_gbs}
@@ -397,7 +411,8 @@ def run_ours(args, ws, rank, local):
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "roofline": roof, "hbm_roofline": hbm_roof,
            "kernels_ms": {"fill_guards": t_fill, "cfl_dt": t_cfl, "step": t_step},
-           "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2},
+           "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2,
+                               "path": "guard fill + CFL dt + one step launch per patch, eager"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "setup_s": {"generate": t_gen}}
     if rank == 0 and not args.no_extra:

@@ -206,6 +206,16 @@ int mhd_cfl_dt_uniform_noalloc(const void *state, int real_bytes, int npatch, in
                                int nz, int guard, const double dx[3], double gamma,
                                double courant, void *dt_dev, void *cuda_stream);
 
+/* Attainable SIMT fused multiply-add rate of the current device, the denominator of the
+ * arithmetic roofline of the fused step (which has no dense contraction and runs on the
+ * FP32 / FP64 SIMT pipes, not on the tensor cores).  Runs independent FMA chains on four
+ * 256-thread blocks per SM on cuda_stream (NULL: legacy default stream), one warm-up and
+ * three timed launches, synchronising the stream; writes the best rate, counting 2 flops
+ * per FMA, to *flops_per_second.  real_bytes 4 (FP32) or 8 (FP64).  Takes tens of
+ * milliseconds (FP32) and allocates nothing.  MHD_EINVAL for a bad argument (checked
+ * before any device call), MHD_ECUDA for a CUDA error. */
+int mhd_probe_fma_rate(int real_bytes, void *cuda_stream, double *flops_per_second);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ UNITS = {
     "kernels_f64.cu": [],
     "mhd_bunch.cu": [],
     "mhd_noalloc.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "mhd_probe.cu": [],
 }
 
 

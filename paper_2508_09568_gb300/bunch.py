@@ -164,3 +164,15 @@ class MHDBunch:
             self.close()
         except Exception:
             pass
+
+
+def fma_rate(dtype=torch.float32, device="cuda") -> float:
+    """Attainable SIMT FMA rate (flop/s, 2 per FMA) of the device, measured by the
+    library's probe kernel on a fresh stream (mhd_probe_fma_rate)."""
+    lib = capi.load()
+    rb = 4 if dtype == torch.float32 else 8
+    with torch.cuda.device(torch.device(device)):
+        st = torch.cuda.Stream()
+        r = ct.c_double()
+        capi.check(lib.mhd_probe_fma_rate(rb, ct.c_void_p(st.cuda_stream), ct.byref(r)))
+    return r.value

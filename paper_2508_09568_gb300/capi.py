@@ -55,6 +55,7 @@ SIGNATURES = {
     "mhd_bunch_destroy": (None, [P]),
     "mhd_last_error": (ct.c_char_p, []),
     "mhd_cfl_dt_uniform_noalloc": (I, [P, I, I, I, I, I, I, DP, D, D, P, P]),
+    "mhd_probe_fma_rate": (I, [I, P, DP]),
 }
 MHD_NOALLOC_MAX_PATCHES = 16384
 

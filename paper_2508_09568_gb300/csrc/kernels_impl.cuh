@@ -51,10 +51,14 @@ struct StepInst {
 };
 
 template <typename R>
-static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, const FillGeom& fg, unsigned* err,
-                               cudaStream_t s) {
-    dim3 grid(8, npatch < 65535 ? npatch : 65535);
-    fill_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U), patches, npatch, fg, err);
+static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, const FillGeom& fg,
+                               const int64_t* nboff, int Zp, unsigned* err, cudaStream_t s) {
+    if (nboff) {
+        fill_grid_kernel<R><<<(unsigned)npatch * (unsigned)Zp, 128, 0, s>>>(static_cast<R*>(U), patches, nboff, Zp);
+    } else {
+        dim3 grid(8, npatch < 65535 ? npatch : 65535);
+        fill_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U), patches, npatch, fg, err);
+    }
     return cudaGetLastError();
 }
 

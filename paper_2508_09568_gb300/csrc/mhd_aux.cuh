@@ -87,6 +87,46 @@ __global__ void fill_kernel(R* __restrict__ U, const PatchDev* __restrict__ patc
     }
 }
 
+// a1 for bunches of equal patches on a regular grid (the same values as fill_kernel): the
+// source of every ghost cell comes from the patch's neighbour table instead of the owner
+// map.  One CTA per padded z-plane of a patch (blockIdx.x = patch * Z + plane) walks only
+// the plane's ghost cells: the whole plane outside the interior z range, else the ghost
+// rows (taken whole) and the ghost columns of the interior rows.
+template <typename R>
+__global__ void __launch_bounds__(128) fill_grid_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
+                                                       const int64_t* __restrict__ nboff, int Zp) {
+    const int p = blockIdx.x / Zp, z = blockIdx.x - p * Zp;
+    const PatchDev pt = patches[p];
+    const int64_t* nb = nboff + (int64_t)p * 27;
+    const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy;
+    const int64_t vol = (int64_t)X * Y * pt.Z;
+    const int iz = z - pt.gz;
+    const bool zghost = iz < 0 || iz >= pt.nz;
+    const int nfull = zghost ? X * Y : 2 * gy * X;
+    const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
+    R* plane = U + pt.off + (int64_t)z * X * Y;
+    for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
+        int x, y;
+        if (k < nfull) {
+            const int r = k / X;
+            x = k - r * X;
+            y = zghost ? r : (r < gy ? r : pt.ny + r);
+        } else {
+            const int k2 = k - nfull;
+            const int r = k2 / (2 * gx), c = k2 - r * (2 * gx);
+            y = gy + r;
+            x = c < gx ? c : pt.nx + c;
+        }
+        const R* s = U + neighbour_source(pt, nb, x - gx, y - gy, iz);
+        R* d = plane + (int64_t)y * X + x;
+        R v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = s[q * vol];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q * vol] = v[q];
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // a2: CFL time step.  rate = sum over active axes of (|u_d| + c_f,d) / dx_d per interior
 // cell; each block reduces its patches' maximum (warp shuffles, then shared memory) into

@@ -63,6 +63,9 @@ struct mhd_bunch {
     PatchDev* d_patches = nullptr;
     int* d_owner = nullptr;
     FillGeom fg{};
+    // neighbour offsets [npatch][27] of the table-driven guard fill (equal patches on a
+    // regular grid only; null otherwise)
+    int64_t* d_nboff = nullptr;
     // tiles of each step configuration: natural (per patch) order and cost-sorted order
     struct Tiles {
         int4* d_nat = nullptr;
@@ -172,7 +175,7 @@ int common_create(const int32_t* pn, int npatch, int guard, int nvar, int rb, mh
         q.Z = q.nz + 2 * q.gz;
         q.off = off;
         q.ox = q.oy = q.oz = 0;
-        q.pad = 0;
+        q.clamp = 0;
         b->offs[p] = off;
         off += 8LL * q.X * q.Y * q.Z;
         // keep every patch 16-byte aligned
@@ -271,9 +274,46 @@ int ready(const mhd_bunch* b) {
 }
 
 int do_fill(mhd_bunch* b) {
-    CK(b->K->fill(b->buf[b->cur], b->d_patches, b->npatch, b->fg, b->d_err, b->stream));
+    CK(b->K->fill(b->buf[b->cur], b->d_patches, b->npatch, b->fg, b->d_nboff, b->hp[0].Z, b->d_err, b->stream));
     b->launches++;
     return MHD_OK;
+}
+
+// Neighbour table of the table-driven guard fill, for bunches of equal patches (each at
+// least `guard` cells on active axes) whose origins lie on the grid of the patch extent:
+// for every patch and direction s in {-1,0,1}^3 the state offset of the patch owning the
+// cell origin + s * n, wrapped periodically into the box.  Entries of directions that
+// cross an outflow box face are never read (the fill clamps there instead); a collapsed
+// axis only has s = 0 (other entries hold the patch itself).  Empty when the geometry does
+// not qualify (the owner-map fill is used then).
+std::vector<int64_t> neighbour_table(const mhd_bunch* b, const int64_t* origin, const int64_t* N,
+                                     const std::vector<int>& owner, const int64_t* bs, const int64_t* M) {
+    std::vector<int64_t> t;
+    const int n[3] = {b->pn[0], b->pn[1], b->pn[2]};
+    for (int p = 0; p < b->npatch; ++p)
+        for (int d = 0; d < 3; ++d) {
+            if (b->pn[3 * p + d] != n[d]) return t;
+            if (n[d] > 1 && (n[d] < b->guard || origin[3 * p + d] % n[d] != 0 || N[d] % n[d] != 0)) return t;
+        }
+    t.assign((size_t)b->npatch * 27, 0);
+    for (int p = 0; p < b->npatch; ++p)
+        for (int sz = -1; sz <= 1; ++sz)
+            for (int sy = -1; sy <= 1; ++sy)
+                for (int sx = -1; sx <= 1; ++sx) {
+                    const int s[3] = {sx, sy, sz};
+                    int64_t c[3];
+                    bool used = true;
+                    for (int d = 0; d < 3; ++d) {
+                        if (n[d] == 1 && s[d] != 0) used = false;
+                        c[d] = origin[3 * p + d] + (int64_t)s[d] * n[d];
+                        if (c[d] < 0) c[d] += N[d];
+                        else if (c[d] >= N[d]) c[d] -= N[d];
+                    }
+                    int q = p;
+                    if (used) q = owner[(size_t)(((c[2] / bs[2]) * M[1] + c[1] / bs[1]) * M[0] + c[0] / bs[0])];
+                    t[(size_t)p * 27 + (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)] = b->offs[q];
+                }
+    return t;
 }
 
 int do_cfl(mhd_bunch* b, double* dt_dev) {
@@ -433,6 +473,24 @@ int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patc
         b->hp[p].ox = (int)patch_origin[3 * p];
         b->hp[p].oy = (int)patch_origin[3 * p + 1];
         b->hp[p].oz = (int)patch_origin[3 * p + 2];
+        // the patch's sides that are outflow box faces (zero-gradient ghosts)
+        int cl = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (b->pn[3 * p + d] == 1) continue;
+            if (bc[2 * d] == MHD_BC_OUTFLOW && patch_origin[3 * p + d] == 0) cl |= 1 << (2 * d);
+            if (bc[2 * d + 1] == MHD_BC_OUTFLOW && patch_origin[3 * p + d] + b->pn[3 * p + d] == domain_cells[d])
+                cl |= 2 << (2 * d);
+        }
+        b->hp[p].clamp = cl;
+    }
+    {
+        const std::vector<int64_t> t = neighbour_table(b, patch_origin, domain_cells, owner, bs, M);
+        cudaFree(b->d_nboff);
+        b->d_nboff = nullptr;
+        if (!t.empty()) {
+            CK(cudaMalloc(&b->d_nboff, sizeof(int64_t) * t.size()));
+            CK(cudaMemcpy(b->d_nboff, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice));
+        }
     }
     CK(cudaMemcpy(b->d_patches, b->hp.data(), sizeof(PatchDev) * b->npatch, cudaMemcpyHostToDevice));
     int rc = build_tiles(b);
@@ -747,6 +805,7 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     free_tiles(b);
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
+    cudaFree(b->d_nboff);
     cudaFree(b->d_work);
     cudaFree(b->d_partial);
     cudaFree(b->d_counter);

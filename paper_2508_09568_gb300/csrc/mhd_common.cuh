@@ -13,8 +13,42 @@ struct PatchDev {
     int X, Y, Z;          // padded extents (active + 2 * ghost on active axes)
     int gx, gy, gz;       // ghost widths
     int ox, oy, oz;       // global index of the first active cell
-    int pad;
+    int clamp;            // bit 2d / 2d+1: the patch's low / high side on axis d is an outflow box face
 };
+
+// Source of a ghost cell for bunches of equal patches on a regular grid: element offset in
+// the state of the box cell standing at interior-relative coordinates (ix, iy, iz) of patch
+// pt (at most one patch extent outside it on each axis), i.e. the cell the guard fill
+// copies: in the neighbouring patch (nb[27]: element offsets of the 27 neighbours,
+// direction (sx, sy, sz) at (sz+1)*9 + (sy+1)*3 + sx+1, periodic wrap applied), or the
+// nearest cell of the patch itself across an outflow box face (zero gradient).
+__device__ __forceinline__ int64_t neighbour_source(const PatchDev& pt, const int64_t* __restrict__ nb, int ix,
+                                                    int iy, int iz) {
+    int sx = 0, sy = 0, sz = 0;
+    if (ix < 0) {
+        if (pt.clamp & 1) ix = 0;
+        else { sx = -1; ix += pt.nx; }
+    } else if (ix >= pt.nx) {
+        if (pt.clamp & 2) ix = pt.nx - 1;
+        else { sx = 1; ix -= pt.nx; }
+    }
+    if (iy < 0) {
+        if (pt.clamp & 4) iy = 0;
+        else { sy = -1; iy += pt.ny; }
+    } else if (iy >= pt.ny) {
+        if (pt.clamp & 8) iy = pt.ny - 1;
+        else { sy = 1; iy -= pt.ny; }
+    }
+    if (iz < 0) {
+        if (pt.clamp & 16) iz = 0;
+        else { sz = -1; iz += pt.nz; }
+    } else if (iz >= pt.nz) {
+        if (pt.clamp & 32) iz = pt.nz - 1;
+        else { sz = 1; iz -= pt.nz; }
+    }
+    return nb[(sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)] +
+           ((int64_t)(iz + pt.gz) * pt.Y + (iy + pt.gy)) * pt.X + (ix + pt.gx);
+}
 
 // Geometry needed by the guard fill: box extent, boundary kinds and the owner map
 // (a coarse grid of blocks of bs cells, each naming the patch that owns it).

@@ -37,8 +37,10 @@ struct AdjHostArgs {
 struct PrecisionKernels {
     const StepLaunch* step;
     int nstep;
-    cudaError_t (*fill)(void* U, const PatchDev* patches, int npatch, const FillGeom& fg, unsigned* err,
-                        cudaStream_t s);
+    // nboff: neighbour table of a regular grid of equal patches of Zp padded z-planes
+    // (table-driven fill), or null (owner-map fill)
+    cudaError_t (*fill)(void* U, const PatchDev* patches, int npatch, const FillGeom& fg, const int64_t* nboff,
+                        int Zp, unsigned* err, cudaStream_t s);
     // partial: at least cfl_grid reals; counter: one zeroed unsigned
     cudaError_t (*cfl)(const void* U, const PatchDev* patches, int npatch, double gamma, double courant,
                        const double dxi[3], const int act[3], void* partial, int grid, unsigned* counter,

@@ -82,6 +82,23 @@ def test_guard_fill_outflow_bit_exact():
     assert np.array_equal(got.astype(np.float64), ref)
 
 
+def test_guard_fill_every_boundary_combination_bit_exact():
+    """Equal patches on a regular grid use the neighbour-table fill: bit exact against the
+    oracle's fill for all 64 periodic / outflow choices of the six box faces (a box with a
+    single patch along y, so its neighbours there are itself)."""
+    import itertools
+    g0, U, meta = W.small_box(ncell=(16, 8, 16), patch=(8, 8, 8), seed=13)
+    for bcx in itertools.product((W.BC_PERIODIC, W.BC_OUTFLOW), repeat=6):
+        geom = W.uniform_geometry([16, 8, 16], [8, 8, 8], dx=g0.dx,
+                                  bc=[[bcx[0], bcx[1]], [bcx[2], bcx[3]], [bcx[4], bcx[5]]])
+        flat = W.to_patches(U, geom)
+        b = gpu_bunch(geom, flat, meta["gamma"], torch.float64)
+        b.fill_guards()
+        ob = oracle_bunch(geom, meta["gamma"])
+        assert np.array_equal(b.download(), ob.join(ob.fill_guards(ob.split(flat)))), bcx
+        b.close()
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-14), (torch.float32, 2e-6)], ids=["f64", "f32"])
 def test_cfl_dt_matches_oracle(dtype, tol):
     for geom, U, meta in (W.small_box(seed=2), W.orszag_tang(ncell=64, patch=16), W.sod(64, 4)):
