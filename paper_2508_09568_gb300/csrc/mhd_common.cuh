@@ -6,7 +6,7 @@
 
 namespace mhd {
 
-// Device patch-table entry (one per patch, about 48 bytes).
+// Device patch-table entry (one per patch, 64 bytes).
 struct PatchDev {
     int64_t off;          // element offset of the patch in the state buffer
     int nx, ny, nz;       // active cells
