@@ -4,6 +4,7 @@
 namespace mhd {
 
 static const StepLaunch kStepF32[] = {
+    StepInst<float, 3, 16, 16, 512, 1, true>::entry(),
     StepInst<float, 3, 16, 16, 512>::entry(),
     StepInst<float, 3, 16, 8, 256, 2>::entry(),
     StepInst<float, 3, 8, 8, 128, 3>::entry(),

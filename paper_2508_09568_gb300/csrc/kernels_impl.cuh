@@ -28,21 +28,21 @@ static StepArgs<R> to_args(const StepHostArgs& h) {
     return a;
 }
 
-template <typename R, int NDIM, int TX, int TY, int NT, int MINB = 1>
+template <typename R, int NDIM, int TX, int TY, int NT, int MINB = 1, bool PREFETCH = false>
 struct StepInst {
     using C = StepCfg<R, NDIM, TX, TY, NT>;
     static_assert(C::SMEM_BYTES * MINB <= 227 * 1024, "tile too large for shared memory");
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT, MINB>,
+        return cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
     }
     static cudaError_t occupancy(int* blocks) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_kernel<R, NDIM, TX, TY, NT, MINB>, NT,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH>, NT,
                                                              C::SMEM_BYTES);
     }
     static cudaError_t launch(const void* args, int grid, cudaStream_t s) {
         const StepArgs<R> a = to_args<R>(*static_cast<const StepHostArgs*>(args));
-        step_kernel<R, NDIM, TX, TY, NT, MINB><<<grid, NT, C::SMEM_BYTES, s>>>(a);
+        step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH><<<grid, NT, C::SMEM_BYTES, s>>>(a);
         return cudaGetLastError();
     }
     static StepLaunch entry() {

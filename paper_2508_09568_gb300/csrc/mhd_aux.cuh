@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(128) fill_grid_kernel(R* __restrict__ U, const
     const int nfull = zghost ? X * Y : 2 * gy * X;
     const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
     R* plane = U + pt.off + (int64_t)z * X * Y;
-    for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
-        int x, y;
+    // plane coordinates of the k-th ghost cell of the plane
+    auto coord = [&](int k, int& x, int& y) {
         if (k < nfull) {
             const int r = k / X;
             x = k - r * X;
@@ -117,13 +117,29 @@ __global__ void __launch_bounds__(128) fill_grid_kernel(R* __restrict__ U, const
             y = gy + r;
             x = c < gx ? c : pt.nx + c;
         }
-        const R* s = U + neighbour_source(pt, nb, x - gx, y - gy, iz);
-        R* d = plane + (int64_t)y * X + x;
-        R v[8];
+    };
+    // two cells per thread and iteration: all 16 loads in flight before the stores
+    for (int k0 = threadIdx.x; k0 < ncnt; k0 += 2 * blockDim.x) {
+        const int k1 = k0 + blockDim.x;
+        const bool two = k1 < ncnt;
+        int x0, y0, x1 = 0, y1 = 0;
+        coord(k0, x0, y0);
+        if (two) coord(k1, x1, y1);
+        const R* s0 = U + neighbour_source(pt, nb, x0 - gx, y0 - gy, iz);
+        const R* s1 = two ? U + neighbour_source(pt, nb, x1 - gx, y1 - gy, iz) : s0;
+        R v0[8], v1[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = s[q * vol];
+        for (int q = 0; q < 8; ++q) v0[q] = s0[q * vol];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) d[q * vol] = v[q];
+        for (int q = 0; q < 8; ++q) v1[q] = s1[q * vol];
+        R* d0 = plane + (int64_t)y0 * X + x0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d0[q * vol] = v0[q];
+        if (two) {
+            R* d1 = plane + (int64_t)y1 * X + x1;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) d1[q * vol] = v1[q];
+        }
     }
 }
 
@@ -190,7 +206,7 @@ __global__ void cfl_kernel(CflArgs<R> a) {
             const R bzc = a.act[2] ? R(0.5) * (c[7 * vol] + c[7 * vol + sz]) : c[7 * vol];
             R q[8];
             cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
-            const R ri = R(1) / q[Q_RHO], gP = gamma * q[Q_P];
+            const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
             R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
             if (a.act[1]) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
             if (a.act[2]) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;

@@ -29,6 +29,19 @@ MHD_HD R rabs(R x) { return x < R(0) ? -x : x; }
 MHD_HD float rsqrt_(float x) { return sqrtf(x); }
 MHD_HD double rsqrt_(double x) { return sqrt(x); }
 
+// Quotient.  Single precision on the device: the hardware approximate division
+// (__fdividef, a reciprocal and a multiply, within 2 ulp for divisors below 2^126 in
+// magnitude, which every divisor of the scheme is); double precision and host code: the
+// IEEE operation.
+MHD_HD float rdiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+MHD_HD double rdiv(double a, double b) { return a / b; }
+
 // max/min with ties going to the first argument (the subgradient choice of the adjoint)
 template <typename R>
 MHD_HD R fmax1(R a, R b) { return a >= b ? a : b; }
@@ -69,7 +82,7 @@ MHD_HD R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
 template <typename R>
 MHD_HD void cons_to_prim(R rho, R mx, R my, R mz, R E, R bxc, R byc, R bzc,
                                              R gm1, R q[8]) {
-    R ri = R(1) / rho;
+    R ri = rdiv(R(1), rho);
     R u = mx * ri, v = my * ri, w = mz * ri;
     q[Q_RHO] = rho;
     q[Q_U] = u;
@@ -90,7 +103,7 @@ template <typename R>
 MHD_HD void hancock(const R q[8], const R D[3][8], R hdt, R gamma, R out[5]) {
     const R u = q[Q_U], v = q[Q_V], w = q[Q_W], rho = q[Q_RHO], P = q[Q_P];
     const R divu = D[0][Q_U] + D[1][Q_V] + D[2][Q_W];
-    const R ri = R(1) / rho;
+    const R ri = rdiv(R(1), rho);
 #define ADV(k) (u * D[0][k] + v * D[1][k] + w * D[2][k])
     out[0] = rho - hdt * (ADV(Q_RHO) + rho * divu);
     out[4] = P - hdt * (ADV(Q_P) + gamma * P * divu);
@@ -122,23 +135,23 @@ MHD_HD void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps,
     const R ptl = pl + R(0.5) * b2l, ptr = pr + R(0.5) * b2r;
     const R el = pl * gm1i + R(0.5) * rl * (ul * ul + vl * vl + wl * wl) + R(0.5) * b2l;
     const R er = pr * gm1i + R(0.5) * rr * (ur * ur + vr * vr + wr * wr) + R(0.5) * b2r;
-    const R cfl = fast_speed(R(1) / rl, gamma * pl, bn, byl, bzl);
-    const R cfr = fast_speed(R(1) / rr, gamma * pr, bn, byr, bzr);
+    const R cfl = fast_speed(rdiv(R(1), rl), gamma * pl, bn, byl, bzl);
+    const R cfr = fast_speed(rdiv(R(1), rr), gamma * pr, bn, byr, bzr);
     const R vbl = ul * bn + vl * byl + wl * bzl, vbr = ur * bn + vr * byr + wr * bzr;
     const R cmax = fmax1(cfl, cfr);
     const R sl = fmin1(ul, ur) - cmax;
     const R sr = fmax1(ul, ur) + cmax;
     const R dl = (sl - ul) * rl, dr = (sr - ur) * rr;
-    const R deni = R(1) / (dr - dl);
+    const R deni = rdiv(R(1), dr - dl);
     const R sm = (dr * ur - dl * ul - ptr + ptl) * deni;
     const R pts = (dr * ptl - dl * ptr + dl * dr * (ur - ul)) * deni;
 
     // star states
-    const R sli = R(1) / (sl - sm), sri = R(1) / (sr - sm);
+    const R sli = rdiv(R(1), sl - sm), sri = rdiv(R(1), sr - sm);
     const R rsl = rl * (sl - ul) * sli, rsr = rr * (sr - ur) * sri;
     const R Dl = rl * (sl - ul) * (sl - sm) - bn2, Dr = rr * (sr - ur) * (sr - sm) - bn2;
     const bool degl = rabs(Dl) <= eps * bn2, degr = rabs(Dr) <= eps * bn2;
-    const R Dli = degl ? R(0) : R(1) / Dl, Dri = degr ? R(0) : R(1) / Dr;
+    const R Dli = degl ? R(0) : rdiv(R(1), Dl), Dri = degr ? R(0) : rdiv(R(1), Dr);
     const R nul = bn * (sm - ul) * Dli, nur = bn * (sm - ur) * Dri;
     const R nbl = (rl * (sl - ul) * (sl - ul) - bn2) * Dli, nbr = (rr * (sr - ur) * (sr - ur) - bn2) * Dri;
     const R vsl = degl ? vl : vl - byl * nul, wsl = degl ? wl : wl - bzl * nul;
@@ -152,9 +165,9 @@ MHD_HD void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps,
     // double-star states
     const R sql = rsqrt_(rsl), sqr = rsqrt_(rsr);
     const R abn = rabs(bn);
-    const R ssl = sm - abn / sql, ssr = sm + abn / sqr;
+    const R ssl = sm - rdiv(abn, sql), ssr = sm + rdiv(abn, sqr);
     const R sgn = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0));
-    const R isum = R(1) / (sql + sqr);
+    const R isum = rdiv(R(1), sql + sqr);
     const R vss = (sql * vsl + sqr * vsr + (bysr - bysl) * sgn) * isum;
     const R wss = (sql * wsl + sqr * wsr + (bzsr - bzsl) * sgn) * isum;
     const R byss = (sql * bysr + sqr * bysl + sql * sqr * (vsr - vsl) * sgn) * isum;
@@ -231,7 +244,7 @@ MHD_HD R emf2d(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>& NW,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const Corner<R>& s = *st[k];
-        const R ri = R(1) / s.rho, gP = gamma * s.p;
+        const R ri = rdiv(R(1), s.rho), gP = gamma * s.p;
         const R cfa = fast_speed(ri, gP, s.Ba, s.Bb, s.Be);
         const R cfb = fast_speed(ri, gP, s.Bb, s.Ba, s.Be);
         ap[k] = s.ua + cfa;
@@ -249,7 +262,7 @@ MHD_HD R emf2d(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>& NW,
     const R eNW = NW.ua * NW.Bb - NW.ub * NW.Ba;
     const R eNE = NE.ua * NE.Bb - NE.ub * NE.Ba;
     const R num = sE * sN * eSW - sE * sS * eNW - sW * sN * eSE + sW * sS * eNE;
-    return num / (da * db) + sE * sW / da * (SE.Bb - SW.Bb) - sN * sS / db * (NW.Ba - SW.Ba);
+    return rdiv(num, da * db) + rdiv(sE * sW, da) * (SE.Bb - SW.Bb) - rdiv(sN * sS, db) * (NW.Ba - SW.Ba);
 }
 
 }  // namespace mhd

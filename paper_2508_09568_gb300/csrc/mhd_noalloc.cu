@@ -96,7 +96,7 @@ __global__ void cfl_uniform_kernel(const R* __restrict__ U, int npatch, int nx, 
         const R bzc = az ? R(0.5) * (c[7 * vol] + c[7 * vol + (int64_t)X * Y]) : c[7 * vol];
         R q[8];
         cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
-        const R ri = R(1) / q[Q_RHO], gP = gamma * q[Q_P];
+        const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
         R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
         if (ay) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
         if (az) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;

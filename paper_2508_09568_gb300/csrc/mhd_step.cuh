@@ -93,9 +93,22 @@ __device__ __forceinline__ int pidx(int i, int j) {   // prep cell index
 }
 
 // ---------------------------------------------------------------------------------------
-// stage 1: load one plane of U^n into the W ring (raw), and the next plane's Bz
+// stage 1: load one plane of U^n into the W ring (raw), and the next plane's Bz.
+// ASYNC: element copies global -> shared with cp.async (the issuing threads do not wait;
+// cp_async_wait_all before the barrier that publishes the plane), so that the copies of
+// plane m+1 can be issued before the flux stage of plane m-1 and complete under it.
 // ---------------------------------------------------------------------------------------
-template <typename R, typename C>
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* smem_dst, const R* gsrc) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename R, typename C, bool ASYNC = false>
 __device__ __forceinline__ void stage_load(const R* __restrict__ U, const PatchDev& pt, int x0, int y0,
                                            int m, R* Wslot, R* bznext) {
     const int gx = pt.gx, gy = pt.gy, gz = pt.gz;
@@ -109,21 +122,25 @@ __device__ __forceinline__ void stage_load(const R* __restrict__ U, const PatchD
         const bool in = x >= 0 && x < X && y >= 0 && y < Y && z >= 0 && z < Z;
         if (in) {
             const int64_t o = ((int64_t)z * Y + y) * X + x;
-            Wslot[0 * C::LSZ + w] = base[0 * vol + o];
-            Wslot[1 * C::LSZ + w] = base[1 * vol + o];
-            Wslot[2 * C::LSZ + w] = base[2 * vol + o];
-            Wslot[3 * C::LSZ + w] = base[3 * vol + o];
-            Wslot[4 * C::LSZ + w] = base[4 * vol + o];
-            Wslot[8 * C::LSZ + w] = base[5 * vol + o];
-            Wslot[9 * C::LSZ + w] = base[6 * vol + o];
-            Wslot[10 * C::LSZ + w] = base[7 * vol + o];
-            R bzn;
-            if (C::AZ) {
-                bzn = (z + 1 < Z) ? base[7 * vol + o + (int64_t)X * Y] : R(0);
+            const bool hasnext = C::AZ ? (z + 1 < Z) : true;
+            const R* nxt = base + 7 * vol + o + (C::AZ ? (int64_t)X * Y : 0);
+            if constexpr (ASYNC) {
+                constexpr int dst[8] = {0, 1, 2, 3, 4, 8, 9, 10};
+#pragma unroll
+                for (int v = 0; v < 8; ++v) cp_async_elem(&Wslot[dst[v] * C::LSZ + w], base + v * vol + o);
+                if (hasnext) cp_async_elem(&bznext[w], nxt);
+                else bznext[w] = R(0);
             } else {
-                bzn = base[7 * vol + o];
+                Wslot[0 * C::LSZ + w] = base[0 * vol + o];
+                Wslot[1 * C::LSZ + w] = base[1 * vol + o];
+                Wslot[2 * C::LSZ + w] = base[2 * vol + o];
+                Wslot[3 * C::LSZ + w] = base[3 * vol + o];
+                Wslot[4 * C::LSZ + w] = base[4 * vol + o];
+                Wslot[8 * C::LSZ + w] = base[5 * vol + o];
+                Wslot[9 * C::LSZ + w] = base[6 * vol + o];
+                Wslot[10 * C::LSZ + w] = base[7 * vol + o];
+                bznext[w] = hasnext ? *nxt : R(0);
             }
-            bznext[w] = bzn;
         } else {
             // outside the padded patch: a benign state, never used by owned outputs
             Wslot[0 * C::LSZ + w] = R(1);
@@ -424,7 +441,10 @@ __device__ __forceinline__ void stage_update(const StepSmem<R, C>& S, const R* _
     }
 }
 
-template <typename R, int NDIM, int TX, int TY, int NT, int MINB>
+// PREFETCH (3D): the raw plane m+1 is copied with cp.async into the W-ring slot of plane
+// c-1 (free once plane c is prepared) while the flux stage of plane c runs, instead of
+// being loaded at the start of the next iteration.
+template <typename R, int NDIM, int TX, int TY, int NT, int MINB, bool PREFETCH>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     using C = StepCfg<R, NDIM, TX, TY, NT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -470,14 +490,18 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
         X.dxi[2] = R(a.dxi[2]);
         X.limiter = a.limiter;
 
+        constexpr bool PF = PREFETCH && C::AZ;
         for (int s = 0; s < niter; ++s) {
             const int m = C::AZ ? s - 2 : 0;     // plane loaded
             const int c = C::AZ ? s - 3 : 0;     // plane prepared
-            // ---- load plane m (+ the update of plane s-5, which reads only flux buffers)
+            // ---- load plane m (+ the update of plane s-5, which reads only flux buffers);
+            // with the prefetch, plane m was issued in the previous iteration's flux stage
             R* Wm_slot = S.W(C::AZ ? (m + 3) % 3 : 0);
-            if (!C::AZ || m <= nz + 1) stage_load<R, C>(a.U, pt, x0, y0, m, Wm_slot, bznext);
+            if ((!PF || s == 0) && (!C::AZ || m <= nz + 1))
+                stage_load<R, C, PF>(a.U, pt, x0, y0, m, Wm_slot, bznext);
             if (C::AZ && s >= 5)
                 stage_update<R, C>(S, a.U, a.Unew, pt, x0, y0, s - 5, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
+            if (PF) cp_async_wait_all();
             __syncthreads();
             if (C::AZ && m > nz + 1) break;      // the last update is done
             stage_convert<R, C>(Wm_slot, bznext, gm1);
@@ -496,6 +520,8 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
                 }
             }
             __syncthreads();
+            // ---- prefetch plane m+1 into the slot of plane c-1 (read by nobody from here on)
+            if (PF && m + 1 <= nz + 1) stage_load<R, C, true>(a.U, pt, x0, y0, m + 1, S.W((m + 4) % 3), bznext);
             // ---- fluxes of plane c and between planes c-1 and c
             if (c >= 0) {
                 const R* P0 = S.P(C::AZ ? (c + 2) & 1 : 0);
