@@ -152,6 +152,21 @@ int mhd_bunch_graph_launch(mhd_bunch *b);
  * Synchronises the bound stream. */
 int mhd_bunch_advance_host(mhd_bunch *b, void *host_state, int nsteps, double *t_out);
 
+/* Host-resident state streamed through the GPU every step (bunches staged from the host
+ * for each update and returned, Secs. 2.4 and 4 of the paper), with copies overlapped with
+ * the update: the state in host_state (state_size bytes, layout above; page-locked memory
+ * for the copies to overlap) is cut into nchunks contiguous runs of patches.  Per step:
+ * every chunk is copied to the device (on a library-owned stream; chunk k as soon as the
+ * previous step returned it), then guard fill -> CFL dt -> the update chunk by chunk on
+ * the bound stream, each updated chunk copied back into host_state (on a second library
+ * stream) while the next chunk is updated.  After nsteps steps host_state holds the final
+ * state (its ghost cells are not meaningful), the device buffer current afterwards holds
+ * it too, and *t_out (may be NULL) the simulated time.  nsteps >= 1, 1 <= nchunks (more
+ * chunks than patches are capped); the bound stream must not be the legacy default
+ * stream.  Synchronises the bound stream; returns the device error word as
+ * mhd_bunch_get_error would. */
+int mhd_bunch_advance_streamed(mhd_bunch *b, void *host_state, int nsteps, int nchunks, double *t_out);
+
 /* Adjoint of one step at fixed dt (the reverse of mhd_bunch_step, including the guard
  * fill): given U^n (interior valid; ghosts are re-filled internally) and the cotangent
  * lam_next of U^{n+1} (interior cells and owned faces), writes

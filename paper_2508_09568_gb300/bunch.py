@@ -136,6 +136,17 @@ class MHDBunch:
                                                    ct.byref(t)))
         return t.value
 
+    def advance_streamed(self, host_state: torch.Tensor, nsteps: int, nchunks: int = 8) -> float:
+        """nsteps steps of a host-resident state (a contiguous CPU tensor of the state layout,
+        pinned for overlap) streamed through the GPU every step in nchunks chunks; returns the
+        simulated time."""
+        assert host_state.device.type == "cpu" and host_state.is_contiguous()
+        assert host_state.numel() * host_state.element_size() == self.nbytes
+        t = ct.c_double()
+        capi.check(self.lib.mhd_bunch_advance_streamed(self.h, ct.c_void_p(host_state.data_ptr()), nsteps, nchunks,
+                                                       ct.byref(t)))
+        return t.value
+
     def step_adjoint(self, dt: float, U_n: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor):
         for t in (U_n, lam_next, lam):
             assert t.is_cuda and t.dtype == self.dtype and t.numel() * self.rb == self.nbytes

@@ -49,6 +49,7 @@ SIGNATURES = {
     "mhd_bunch_graph_capture": (I, [P, I, P]),
     "mhd_bunch_graph_launch": (I, [P]),
     "mhd_bunch_advance_host": (I, [P, P, I, DP]),
+    "mhd_bunch_advance_streamed": (I, [P, P, I, I, DP]),
     "mhd_bunch_step_adjoint": (I, [P, D, P, P, P]),
     "mhd_bunch_get_error": (I, [P, ct.POINTER(I), ct.c_char_p, ct.c_size_t]),
     "mhd_bunch_launch_count": (I, [P, I64P]),

@@ -89,6 +89,9 @@ struct mhd_bunch {
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;                         // index of the buffer holding U^n
     cudaStream_t stream = nullptr;
+    // host-streamed advance: library-owned copy streams and per-chunk events
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_step, ev_out;
     int mode = MHD_MODE_PERSISTENT, config = -1;
     // captured step sequences; with an odd step count the second starts from the other buffer
     cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -361,6 +364,40 @@ int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
         b->launches++;
     }
     b->cur = 1 - b->cur;
+    return MHD_OK;
+}
+
+// Step of the patches [p0, p1) only (U = current buffer -> the other one), one persistent
+// launch over their tiles in natural order; the buffers are not swapped.
+int do_step_range(mhd_bunch* b, const double* dt_ptr, int p0, int p1) {
+    if (b->cfg_index.empty()) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
+    const int k = b->config < 0 ? default_config(b) : b->config;
+    const StepLaunch& L = step_cfg(b, k);
+    const auto& T = b->tiles[k];
+    const int t0 = T.first[p0], t1 = p1 < b->npatch ? T.first[p1] : T.n;
+    if (t1 <= t0) return MHD_OK;
+    StepHostArgs a = step_args(b, dt_ptr, 0.0);
+    int occ = 1;
+    CK(L.occupancy(&occ));
+    occ = std::max(occ, 1);
+    a.tiles = T.d_nat + t0;
+    a.ntiles = t1 - t0;
+    a.dynamic = 1;
+    CK(L.launch(&a, std::min(t1 - t0, b->nsm * occ), b->stream));
+    b->launches++;
+    return MHD_OK;
+}
+
+int ensure_stream_pipeline(mhd_bunch* b, int nchunks) {
+    if (!b->s_in) CK(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
+    if (!b->s_out) CK(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
+    while ((int)b->ev_in.size() < nchunks) {
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        for (auto& x : e) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        b->ev_in.push_back(e[0]);
+        b->ev_step.push_back(e[1]);
+        b->ev_out.push_back(e[2]);
+    }
     return MHD_OK;
 }
 
@@ -788,6 +825,75 @@ int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t
     return code;
 }
 
+int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int nchunks, double* t_out) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!host_state || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
+    if (b->stream == nullptr) return fail(MHD_EINVAL, "the bound stream must not be the legacy default stream");
+    const int K = std::min(nchunks, b->npatch);
+    if (nsteps > b->d_dts_cap) {
+        cudaFree(b->d_dts);
+        b->d_dts = nullptr;
+        CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
+        b->d_dts_cap = nsteps;
+    }
+    rc = ensure_stream_pipeline(b, K);
+    if (rc) return rc;
+    // chunks: contiguous patch ranges of about equal size; bytes [bo[k], bo[k+1])
+    std::vector<int> pb(K + 1);
+    std::vector<size_t> bo(K + 1);
+    for (int k = 0; k <= K; ++k) {
+        pb[k] = (int)((int64_t)b->npatch * k / K);
+        bo[k] = pb[k] < b->npatch ? (size_t)b->offs[pb[k]] * b->rb : b->state_bytes;
+    }
+    char* host = static_cast<char*>(host_state);
+    const int A = b->cur, B = 1 - A;
+    char* dA = static_cast<char*>(b->buf[A]);
+    char* dB = static_cast<char*>(b->buf[B]);
+    // the copy streams start after the work already queued on the bound stream
+    CK(cudaEventRecord(b->ev_step[0], b->stream));
+    CK(cudaStreamWaitEvent(b->s_in, b->ev_step[0], 0));
+    CK(cudaStreamWaitEvent(b->s_out, b->ev_step[0], 0));
+    for (int s = 0; s < nsteps; ++s) {
+        // upload: chunk k of the host state, once the previous step's chunk k is back
+        for (int k = 0; k < K; ++k) {
+            if (s > 0) CK(cudaStreamWaitEvent(b->s_in, b->ev_out[k], 0));
+            CK(cudaMemcpyAsync(dA + bo[k], host + bo[k], bo[k + 1] - bo[k], cudaMemcpyHostToDevice, b->s_in));
+            CK(cudaEventRecord(b->ev_in[k], b->s_in));
+        }
+        for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(b->stream, b->ev_in[k], 0));
+        // guard fill and dt need the whole state; the update runs chunk by chunk and each
+        // chunk goes back to the host as soon as it is done
+        b->cur = A;
+        rc = do_fill(b);
+        if (!rc) rc = do_cfl(b, b->d_dts + s);
+        for (int k = 0; k < K && !rc; ++k) {
+            rc = do_step_range(b, b->d_dts + s, pb[k], pb[k + 1]);
+            if (rc) break;
+            CK(cudaEventRecord(b->ev_step[k], b->stream));
+            CK(cudaStreamWaitEvent(b->s_out, b->ev_step[k], 0));
+            CK(cudaMemcpyAsync(host + bo[k], dB + bo[k], bo[k + 1] - bo[k], cudaMemcpyDeviceToHost, b->s_out));
+            CK(cudaEventRecord(b->ev_out[k], b->s_out));
+        }
+        if (rc) {
+            b->cur = A;
+            cudaStreamSynchronize(b->s_in);
+            cudaStreamSynchronize(b->s_out);
+            return rc;
+        }
+    }
+    // join: the bound stream waits for the last downloads; B holds the final state
+    for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(b->stream, b->ev_out[k], 0));
+    b->cur = B;
+    std::vector<double> dts(nsteps);
+    CK(cudaMemcpyAsync(dts.data(), b->d_dts, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, b->stream));
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
+    return code;
+}
+
 int mhd_bunch_get_error(mhd_bunch* b, int* code, char* msg, size_t len) {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     return read_error(b, code, msg, len);
@@ -803,6 +909,10 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     if (!b) return;
     release_graph(b);
     free_tiles(b);
+    for (auto* v : {&b->ev_in, &b->ev_step, &b->ev_out})
+        for (cudaEvent_t e : *v) cudaEventDestroy(e);
+    if (b->s_in) cudaStreamDestroy(b->s_in);
+    if (b->s_out) cudaStreamDestroy(b->s_out);
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);
