@@ -55,6 +55,9 @@ typedef enum {
 
 enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 };
 enum { MHD_LIMITER_MINMOD = 0, MHD_LIMITER_MC = 1 };
+/* Face-flux solver of the update (a7): HLLD (Sec. 2.1.2, the default) or HLL (the simple
+ * solver of the paper's mockup, Sec. 2.4).  The edge EMF (a8) is the same for both. */
+enum { MHD_RIEMANN_HLLD = 0, MHD_RIEMANN_HLL = 1 };
 
 /* How mhd_bunch_step launches the update kernel.
  *   PER_PATCH  : one launch per patch (the plain path),
@@ -91,6 +94,10 @@ int mhd_bunch_set_geometry(mhd_bunch *b, const double dx[3], const int64_t *patc
 /* Scheme parameters: adiabatic index, Courant number for mhd_bunch_cfl_dt, slope limiter
  * (MHD_LIMITER_MINMOD or MHD_LIMITER_MC).  Defaults: 5/3, 0.8, minmod. */
 int mhd_bunch_set_params(mhd_bunch *b, double gamma, double courant, int limiter);
+
+/* Face-flux solver (MHD_RIEMANN_HLLD or MHD_RIEMANN_HLL) of the step and of its adjoint;
+ * default HLLD.  MHD_EINVAL for another value.  Discards a captured graph. */
+int mhd_bunch_set_riemann(mhd_bunch *b, int solver);
 
 /* Bytes of one state buffer; if patch_offsets is not NULL it receives npatch int64 element
  * offsets (in reals) of the patches inside the buffer. */

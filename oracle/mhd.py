@@ -15,7 +15,8 @@ One step advances every patch of a bunch by the same dt (synchronous time):
   a5  Hancock predictor   Sec. 2.1.4 (primitive Euler half step; face B from the
                           arithmetic edge EMF of Eqs. 7-11, Sec. 2.1.3)
   a6  face states         Sec. 2.1.4
-  a7  HLLD face flux      Sec. 2.1.2 (Miyoshi & Kusano 2005), flux of Eq. 6
+  a7  HLLD face flux      Sec. 2.1.2 (Miyoshi & Kusano 2005), flux of Eq. 6; or the HLL
+                          flux of the paper's mockup solver (Sec. 2.4)
   a8  edge EMF            Sec. 2.1.3, Fig. 3 (corner states LB/RB/LT/RT -> SW/SE/NW/NE,
                           two-dimensional HLL upwind EMF)
   a9  update              finite-volume update of rho, rho*u, E; constrained transport
@@ -55,6 +56,7 @@ F64 = torch.float64
 RHO, MX, MY, MZ, EN, BX, BY, BZ = range(8)
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 LIMITER_MINMOD, LIMITER_MC = 0, 1
+RIEMANN_HLLD, RIEMANN_HLL = 0, 1      # face-flux solver of a7
 AXIS = {0: -1, 1: -2, 2: -3}     # direction (x, y, z) -> tensor axis
 
 # degenerate-star threshold of the HLLD solver, relative to Bn^2, per arithmetic precision
@@ -309,6 +311,45 @@ def hlld(L, R, bn, gamma, eps):
 
 
 # ----------------------------------------------------------------------------------------
+# a7 variant: HLL face flux (Harten, Lax & van Leer 1983), the simple solver the paper's
+# mockup used before the HLLD solver (Sec. 2.4)
+# ----------------------------------------------------------------------------------------
+
+def hll(L, R, bn, gamma):
+    """HLL flux through a face with normal field bn.
+
+    One intermediate state between the fastest left- and right-going signals, with the
+    same estimates as hlld: S_L = min(u_L, u_R) - max(cf_L, cf_R), S_R = max(u_L, u_R) +
+    max(cf_L, cf_R).  The flux at x/t = 0 is F_L when S_L >= 0, otherwise the HLL flux
+    (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) when S_R >= 0, otherwise F_R.
+    L, R and the result as in hlld.
+    """
+    def conserved_and_flux(S):
+        rho, un, ut1, ut2, P, bt1, bt2 = S
+        b2 = bn * bn + bt1 * bt1 + bt2 * bt2
+        pT = P + 0.5 * b2
+        E = P / (gamma - 1.0) + 0.5 * rho * (un * un + ut1 * ut1 + ut2 * ut2) + 0.5 * b2
+        U = [rho, rho * un, rho * ut1, rho * ut2, E]
+        F = [rho * un,
+             rho * un * un + pT - bn * bn,
+             rho * ut1 * un - bt1 * bn,
+             rho * ut2 * un - bt2 * bn,
+             (E + pT) * un - bn * (un * bn + ut1 * bt1 + ut2 * bt2)]
+        return U, F, fast_speed(rho, P, bn, bt1, bt2, gamma)
+
+    UL, FL, cfl = conserved_and_flux(L)
+    UR, FR, cfr = conserved_and_flux(R)
+    cmax = fmax(cfl, cfr)
+    SL = fmin(L[1], R[1]) - cmax
+    SR = fmax(L[1], R[1]) + cmax
+    out = []
+    for c in range(5):
+        fh = (SR * FL[c] - SL * FR[c] + SL * SR * (UR[c] - UL[c])) / (SR - SL)
+        out.append(torch.where(SL >= 0, FL[c], torch.where(SR >= 0, fh, FR[c])))
+    return out
+
+
+# ----------------------------------------------------------------------------------------
 # a8: two-dimensional HLL upwind EMF at an edge, Sec. 2.1.3 / Fig. 3
 # ----------------------------------------------------------------------------------------
 
@@ -349,8 +390,11 @@ def emf_2d(SW, SE, NW, NE, gamma):
 # one step (a3 - a9) for a batch of padded patches
 # ----------------------------------------------------------------------------------------
 
-def step(Up, dt, active, dx, gamma, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], gvec=None, n=None):
+def step(Up, dt, active, dx, gamma, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], gvec=None, n=None,
+         riemann=RIEMANN_HLLD):
     """Advance padded patches (P, 8, Z, Y, X) by dt; returns the new padded tensor.
+
+    riemann selects the face-flux solver of a7: RIEMANN_HLLD (Sec. 2.1.2) or RIEMANN_HLL.
 
     Only interior cells (and their owned low faces) of the result are meaningful; the
     ghost layers of the result are copies of the input ghosts.
@@ -432,7 +476,7 @@ def step(Up, dt, active, dx, gamma, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], gve
         Rq = minus
         L = [Lq[0], Lq[1 + d], Lq[1 + t1], Lq[1 + t2], Lq[4], Lq[5 + t1], Lq[5 + t2]]
         R = [Rq[0], Rq[1 + d], Rq[1 + t1], Rq[1 + t2], Rq[4], Rq[5 + t1], Rq[5 + t2]]
-        f = hlld(L, R, bh[d], gamma, eps)
+        f = hlld(L, R, bh[d], gamma, eps) if riemann == RIEMANN_HLLD else hll(L, R, bh[d], gamma)
         F = [None] * 5
         F[0], F[4] = f[0], f[4]
         F[1 + d], F[1 + t1], F[1 + t2] = f[1], f[2], f[3]
@@ -500,12 +544,13 @@ def step(Up, dt, active, dx, gamma, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], gve
 class Bunch:
     """Oracle view of a flat bunch buffer (float64), following the shared layout."""
 
-    def __init__(self, geom, gamma, courant=0.8, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8]):
+    def __init__(self, geom, gamma, courant=0.8, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], riemann=RIEMANN_HLLD):
         self.geom = geom
         self.gamma = float(gamma)
         self.courant = float(courant)
         self.limiter = int(limiter)
         self.eps = float(eps)
+        self.riemann = int(riemann)
 
     def split(self, flat):
         g = self.geom
@@ -539,7 +584,7 @@ class Bunch:
         for n, idx in sizes.items():
             batch = torch.stack([filled[i] for i in idx])
             new = step(batch, dt, geom.active, geom.dx, self.gamma, self.limiter, self.eps,
-                       gvec=geom.gvec, n=n)
+                       gvec=geom.gvec, n=n, riemann=self.riemann)
             for j, i in enumerate(idx):
                 res[i] = new[j]
         return res

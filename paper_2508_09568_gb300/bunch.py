@@ -19,10 +19,11 @@ class MHDBunch:
 
     geom     workloads.Geometry (patch sizes, origins, box, dx, boundary kinds, guard)
     dtype    torch.float32 or torch.float64 (arithmetic precision of the kernels)
+    riemann  face-flux solver: capi.MHD_RIEMANN_HLLD (default) or capi.MHD_RIEMANN_HLL
     """
 
     def __init__(self, geom: Geometry, dtype=torch.float32, gamma=5.0 / 3.0, courant=0.8, limiter=0,
-                 device="cuda:0", stream: torch.cuda.Stream | None = None):
+                 device="cuda:0", stream: torch.cuda.Stream | None = None, riemann: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("MHDBunch needs a CUDA device (no CPU fallback)")
         self.lib = capi.load()
@@ -46,6 +47,7 @@ class MHDBunch:
             capi.check(self.lib.mhd_bunch_set_geometry(h, dx.ctypes.data_as(capi.DP), org.ctypes.data_as(capi.I64P),
                                                        dom.ctypes.data_as(capi.I64P), bc.ctypes.data_as(capi.I32P)))
             capi.check(self.lib.mhd_bunch_set_params(h, float(gamma), float(courant), int(limiter)))
+            capi.check(self.lib.mhd_bunch_set_riemann(h, int(riemann)))
             nbytes = ct.c_size_t()
             offs = np.zeros(geom.npatch, dtype=np.int64)
             capi.check(self.lib.mhd_bunch_state_size(h, ct.byref(nbytes), offs.ctypes.data_as(capi.I64P)))

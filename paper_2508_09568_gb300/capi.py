@@ -15,6 +15,7 @@ MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_EPHYS, MHD_EBOUNDS, MHD_ETIMEOUT,
     0, -1, -2, -3, -4, -5, -6, -7
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_LIMITER_MINMOD, MHD_LIMITER_MC = 0, 1
+MHD_RIEMANN_HLLD, MHD_RIEMANN_HLL = 0, 1
 MHD_MODE_PER_PATCH, MHD_MODE_BUNCHED, MHD_MODE_PERSISTENT = 0, 1, 2
 
 STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA", -4: "MHD_EPHYS",
@@ -34,6 +35,7 @@ SIGNATURES = {
     "mhd_bunch_create_ragged": (I, [I32P, I, I, I, I, HP]),
     "mhd_bunch_set_geometry": (I, [P, DP, I64P, I64P, I32P]),
     "mhd_bunch_set_params": (I, [P, D, D, I]),
+    "mhd_bunch_set_riemann": (I, [P, I]),
     "mhd_bunch_state_size": (I, [P, ct.POINTER(ct.c_size_t), I64P]),
     "mhd_bunch_bind": (I, [P, P, P, P]),
     "mhd_bunch_current": (I, [P, HP]),

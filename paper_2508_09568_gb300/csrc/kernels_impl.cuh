@@ -24,6 +24,7 @@ static StepArgs<R> to_args(const StepHostArgs& h) {
     a.eps = h.eps;
     for (int d = 0; d < 3; ++d) a.dxi[d] = h.dxi[d];
     a.limiter = h.limiter;
+    a.riemann = h.riemann;
     a.err = h.err;
     return a;
 }
@@ -101,6 +102,7 @@ static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsi
     a.dt = h.dt;
     for (int d = 0; d < 3; ++d) a.dxi[d] = h.dxi[d];
     a.limiter = h.limiter;
+    a.riemann = h.riemann;
     const int bx = (h.max_cells + 255) / 256 < 64 ? (h.max_cells + 255) / 256 : 64;
     const dim3 grid(bx, h.npatch < 65535 ? h.npatch : 65535), blk(256);
     dim3 fgrid(8, h.npatch < 65535 ? h.npatch : 65535);

@@ -37,6 +37,7 @@ struct AdjArgs {
     double gamma, eps, dt;
     double dxi[3];
     int limiter;
+    int riemann;         // face flux: 0 HLLD, 1 HLL
 };
 
 // cell-field index helper for one patch
@@ -278,7 +279,8 @@ __global__ void adj_faces(AdjArgs<R> a) {
             }
             const R bn = fld(a.F, AF_BH + c, a.ncell)[i];
             R lL[7] = {0, 0, 0, 0, 0, 0, 0}, lR[7] = {0, 0, 0, 0, 0, 0, 0}, lbn = R(0);
-            hlld_vjp(L, Rr, bn, gamma, gm1i, eps, lF, lL, lR, lbn);
+            if (a.riemann == 1) hll_vjp(L, Rr, bn, gamma, gm1i, lF, lL, lR, lbn);
+            else hlld_vjp(L, Rr, bn, gamma, gm1i, eps, lF, lL, lR, lbn);
             for (int n = 0; n < 7; ++n) {
                 const int k = ks[n];
                 aadd(&fld(a.G, AF_WH + k, a.ncell)[im], lL[n]);

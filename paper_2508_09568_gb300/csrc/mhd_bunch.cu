@@ -57,6 +57,7 @@ struct mhd_bunch {
     int bc[6] = {0, 0, 0, 0, 0, 0};
     double gamma = 5.0 / 3.0, courant = 0.8;
     int limiter = 0;
+    int riemann = MHD_RIEMANN_HLLD;
     std::vector<int64_t> offs;
     size_t state_bytes = 0;
     std::vector<PatchDev> hp;
@@ -265,6 +266,7 @@ StepHostArgs step_args(mhd_bunch* b, const double* dt_ptr, double dt_val) {
     a.eps = hlld_eps(b->rb);
     for (int d = 0; d < 3; ++d) a.dxi[d] = 1.0 / b->dx[d];
     a.limiter = b->limiter;
+    a.riemann = b->riemann;
     a.err = b->d_err;
     return a;
 }
@@ -545,6 +547,14 @@ int mhd_bunch_set_params(mhd_bunch* b, double gamma, double courant, int limiter
     b->gamma = gamma;
     b->courant = courant;
     b->limiter = limiter;
+    return MHD_OK;
+}
+
+int mhd_bunch_set_riemann(mhd_bunch* b, int solver) {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (solver != MHD_RIEMANN_HLLD && solver != MHD_RIEMANN_HLL) return fail(MHD_EINVAL, "bad face-flux solver");
+    release_graph(b);
+    b->riemann = solver;
     return MHD_OK;
 }
 
@@ -973,6 +983,7 @@ extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, 
     a.dt = dt;
     for (int d = 0; d < 3; ++d) a.dxi[d] = 1.0 / b->dx[d];
     a.limiter = b->limiter;
+    a.riemann = b->riemann;
     int n = 0;
     CK(b->K->adjoint(a, b->fg, b->d_err, b->stream, &n));
     b->launches += n;

@@ -31,6 +31,7 @@ struct AdjHostArgs {
     double gamma, eps, dt;
     double dxi[3];
     int limiter;
+    int riemann;
 };
 
 // Kernel entry points of one precision (R = float or double).
@@ -68,6 +69,7 @@ struct StepHostArgs {
     double gamma, eps;
     double dxi[3];
     int limiter;
+    int riemann;
     unsigned* err;
 };
 

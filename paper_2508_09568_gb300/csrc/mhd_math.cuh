@@ -222,6 +222,39 @@ MHD_HD void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps,
     F[4] = f4;
 }
 
+// HLL flux (Harten, Lax & van Leer 1983; the simple solver of the paper's mockup, Sec. 2.4)
+// through a face with normal field bn: one intermediate state between the fastest signals
+// S_L, S_R (the same estimates as hlld).  States and result as in hlld; the flux at x/t = 0
+// is F_L when S_L >= 0, the HLL flux when S_R >= 0 > S_L, otherwise F_R.
+template <typename R>
+MHD_HD void hll(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R F[5]) {
+    const R bn2 = bn * bn;
+    const R rl = L[0], ul = L[1], vl = L[2], wl = L[3], pl = L[4], byl = L[5], bzl = L[6];
+    const R rr = Rt[0], ur = Rt[1], vr = Rt[2], wr = Rt[3], pr = Rt[4], byr = Rt[5], bzr = Rt[6];
+    const R b2l = bn2 + byl * byl + bzl * bzl, b2r = bn2 + byr * byr + bzr * bzr;
+    const R ptl = pl + R(0.5) * b2l, ptr = pr + R(0.5) * b2r;
+    const R el = pl * gm1i + R(0.5) * rl * (ul * ul + vl * vl + wl * wl) + R(0.5) * b2l;
+    const R er = pr * gm1i + R(0.5) * rr * (ur * ur + vr * vr + wr * wr) + R(0.5) * b2r;
+    const R cfl = fast_speed(rdiv(R(1), rl), gamma * pl, bn, byl, bzl);
+    const R cfr = fast_speed(rdiv(R(1), rr), gamma * pr, bn, byr, bzr);
+    const R vbl = ul * bn + vl * byl + wl * bzl, vbr = ur * bn + vr * byr + wr * bzr;
+    const R cmax = fmax1(cfl, cfr);
+    const R sl = fmin1(ul, ur) - cmax;
+    const R sr = fmax1(ul, ur) + cmax;
+    const R UL[5] = {rl, rl * ul, rl * vl, rl * wl, el};
+    const R UR[5] = {rr, rr * ur, rr * vr, rr * wr, er};
+    const R FL[5] = {rl * ul, rl * ul * ul + ptl - bn2, rl * vl * ul - byl * bn, rl * wl * ul - bzl * bn,
+                     (el + ptl) * ul - bn * vbl};
+    const R FR[5] = {rr * ur, rr * ur * ur + ptr - bn2, rr * vr * ur - byr * bn, rr * wr * ur - bzr * bn,
+                     (er + ptr) * ur - bn * vbr};
+    const R di = rdiv(R(1), sr - sl);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const R fh = (sr * FL[c] - sl * FR[c] + sl * sr * (UR[c] - UL[c])) * di;
+        F[c] = sl >= R(0) ? FL[c] : (sr >= R(0) ? fh : FR[c]);
+    }
+}
+
 // A predicted state at a cell corner around an edge (Fig. 3): density, gas pressure,
 // the velocity components along the edge's two transverse axes a, b, and the field
 // components along a, b and the edge direction e.

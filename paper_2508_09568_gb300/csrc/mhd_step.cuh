@@ -324,7 +324,7 @@ __device__ __forceinline__ R pv(const R* P, int v, int pid) { return P[v * C::PS
 // slot for d = z).  F receives (rho, mx, my, mz, E) fluxes.
 template <typename R, typename C>
 __device__ __forceinline__ void face_flux(const R* PL, int pidL, const R* PR, int pidR, int d, R gamma,
-                                          R gm1i, R eps, R F[5]) {
+                                          R gm1i, R eps, int riemann, R F[5]) {
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     R L[7], Rr[7];
     const int ks[7] = {Q_RHO, Q_U + d, Q_U + t1, Q_U + t2, Q_P, Q_BX + t1, Q_BX + t2};
@@ -336,7 +336,8 @@ __device__ __forceinline__ void face_flux(const R* PL, int pidL, const R* PR, in
     }
     const R bn = pv<R, C>(PR, PV_BH(d), pidR);
     R f[5];
-    hlld(L, Rr, bn, gamma, gm1i, eps, f);
+    if (riemann == 1) hll(L, Rr, bn, gamma, gm1i, f);
+    else hlld(L, Rr, bn, gamma, gm1i, eps, f);
     F[0] = f[0];
     F[4] = f[4];
     F[1 + d] = f[1];
@@ -382,6 +383,7 @@ struct StepArgs {
     double gamma, eps;
     double dxi[3];
     int limiter;
+    int riemann;          // face flux: 0 HLLD, 1 HLL
     unsigned* err;
 };
 
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
                         const int i = r % C::PX, j = r / C::PX;
                         if (inplane && i <= C::TX && j < C::RFX) {
                             R F[5];
-                            face_flux<R, C>(P0, pidx<C>(i - 1, j), P0, pidx<C>(i, j), 0, gamma, gm1i, eps, F);
+                            face_flux<R, C>(P0, pidx<C>(i - 1, j), P0, pidx<C>(i, j), 0, gamma, gm1i, eps, a.riemann, F);
                             const int o = j * (C::TX + 1) + i;
 #pragma unroll
                             for (int v = 0; v < 5; ++v) Fx[v * C::FXN + o] = F[v];
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
                         const int i = r % C::PX - 1, j = r / C::PX;
                         if (C::AY && inplane && i >= 0 && i < C::TX && j < C::RFY) {
                             R F[5];
-                            face_flux<R, C>(P0, pidx<C>(i, j - 1), P0, pidx<C>(i, j), 1, gamma, gm1i, eps, F);
+                            face_flux<R, C>(P0, pidx<C>(i, j - 1), P0, pidx<C>(i, j), 1, gamma, gm1i, eps, a.riemann, F);
                             const int o = j * C::TX + i;
 #pragma unroll
                             for (int v = 0; v < 5; ++v) Fy[v * C::FYN + o] = F[v];
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
                         if (C::AZ && i >= 0 && i < C::TX && j < C::RFZ) {
                             const int p = pidx<C>(i, j);
                             R F[5];
-                            face_flux<R, C>(Pm, p, P0, p, 2, gamma, gm1i, eps, F);
+                            face_flux<R, C>(Pm, p, P0, p, 2, gamma, gm1i, eps, a.riemann, F);
                             const int o = j * C::TX + i;
 #pragma unroll
                             for (int v = 0; v < 5; ++v) Fz[v * C::FZN + o] = F[v];

@@ -498,6 +498,125 @@ MHD_HD void hlld_vjp(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps, 
     lbn += g_bn;
 }
 
+// d hll: lF[5] -> lL[7], lR[7], lbn.  Same forward sequence as hll(); the region (L, HLL
+// state, R) and the max / min selections of the wave speeds are constant.
+template <typename R>
+MHD_HD void hll_vjp(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, const R lF[5], R lL[7], R lR[7], R& lbn) {
+    // ----- forward (as hll)
+    const R bn2 = bn * bn;
+    const R* st[2] = {L, Rt};
+    R U[2][5], F[2][5], cf[2], e[2], pt[2], vb[2];
+    for (int k = 0; k < 2; ++k) {
+        const R r = st[k][0], u = st[k][1], v = st[k][2], w = st[k][3], p = st[k][4], by = st[k][5], bz = st[k][6];
+        const R b2 = bn2 + by * by + bz * bz;
+        pt[k] = p + R(0.5) * b2;
+        e[k] = p * gm1i + R(0.5) * r * (u * u + v * v + w * w) + R(0.5) * b2;
+        cf[k] = fast_speed(rdiv(R(1), r), gamma * p, bn, by, bz);
+        vb[k] = u * bn + v * by + w * bz;
+        U[k][0] = r;
+        U[k][1] = r * u;
+        U[k][2] = r * v;
+        U[k][3] = r * w;
+        U[k][4] = e[k];
+        F[k][0] = r * u;
+        F[k][1] = r * u * u + pt[k] - bn2;
+        F[k][2] = r * v * u - by * bn;
+        F[k][3] = r * w * u - bz * bn;
+        F[k][4] = (e[k] + pt[k]) * u - bn * vb[k];
+    }
+    const R ul = L[1], ur = Rt[1];
+    const bool cl = cf[0] >= cf[1];
+    const R cmax = cl ? cf[0] : cf[1];
+    const bool ml = ul <= ur, Ml = ul >= ur;
+    const R sl = (ml ? ul : ur) - cmax;
+    const R sr = (Ml ? ul : ur) + cmax;
+    // ----- reverse
+    R lU[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}}, lFs[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    R lsl = R(0), lsr = R(0);
+    if (sl >= R(0)) {
+        for (int c = 0; c < 5; ++c) lFs[0][c] = lF[c];
+    } else if (sr >= R(0)) {
+        const R di = R(1) / (sr - sl);
+        for (int c = 0; c < 5; ++c) {
+            const R dU = U[1][c] - U[0][c];
+            const R fh = (sr * F[0][c] - sl * F[1][c] + sl * sr * dU) * di;
+            lFs[0][c] = lF[c] * sr * di;
+            lFs[1][c] = -lF[c] * sl * di;
+            lU[1][c] = lF[c] * sl * sr * di;
+            lU[0][c] = -lF[c] * sl * sr * di;
+            lsr += lF[c] * (F[0][c] + sl * dU - fh) * di;
+            lsl += lF[c] * (-F[1][c] + sr * dU + fh) * di;
+        }
+    } else {
+        for (int c = 0; c < 5; ++c) lFs[1][c] = lF[c];
+    }
+    // wave speeds: sl = min(ul, ur) - cmax, sr = max(ul, ur) + cmax
+    R* lst[2] = {lL, lR};
+    lst[ml ? 0 : 1][1] += lsl;
+    lst[Ml ? 0 : 1][1] += lsr;
+    const R lcmax = lsr - lsl;
+    R lcf[2] = {cl ? lcmax : R(0), cl ? R(0) : lcmax};
+    for (int k = 0; k < 2; ++k) {
+        const R r = st[k][0], u = st[k][1], v = st[k][2], w = st[k][3], p = st[k][4], by = st[k][5], bz = st[k][6];
+        R lr = R(0), lu = R(0), lv = R(0), lw = R(0), lp = R(0), lby = R(0), lbz = R(0);
+        fast_speed_vjp(r, p, bn, by, bz, gamma, lcf[k], lr, lp, lbn, lby, lbz);
+        const R* g = lFs[k];
+        const R* h = lU[k];
+        // U = (r, r u, r v, r w, e)
+        lr += h[0] + h[1] * u + h[2] * v + h[3] * w;
+        lu += h[1] * r;
+        lv += h[2] * r;
+        lw += h[3] * r;
+        R le = h[4];
+        // F0 = r u
+        lr += g[0] * u;
+        lu += g[0] * r;
+        // F1 = r u^2 + pt - bn^2
+        lr += g[1] * u * u;
+        lu += g[1] * R(2) * r * u;
+        R lpt = g[1];
+        lbn -= g[1] * R(2) * bn;
+        // F2 = r v u - by bn, F3 = r w u - bz bn
+        lr += g[2] * v * u + g[3] * w * u;
+        lv += g[2] * r * u;
+        lw += g[3] * r * u;
+        lu += g[2] * r * v + g[3] * r * w;
+        lby -= g[2] * bn;
+        lbz -= g[3] * bn;
+        lbn -= g[2] * by + g[3] * bz;
+        // F4 = (e + pt) u - bn vb, vb = u bn + v by + w bz
+        le += g[4] * u;
+        lpt += g[4] * u;
+        lu += g[4] * (e[k] + pt[k]);
+        lbn -= g[4] * vb[k];
+        const R lvb = -g[4] * bn;
+        lu += lvb * bn;
+        lbn += lvb * u;
+        lv += lvb * by;
+        lby += lvb * v;
+        lw += lvb * bz;
+        lbz += lvb * w;
+        // e = p/(gamma-1) + r (u^2 + v^2 + w^2)/2 + b2/2, pt = p + b2/2, b2 = bn^2 + by^2 + bz^2
+        lp += le * gm1i + lpt;
+        lr += le * R(0.5) * (u * u + v * v + w * w);
+        lu += le * r * u;
+        lv += le * r * v;
+        lw += le * r * w;
+        const R lb2 = R(0.5) * (le + lpt);
+        lbn += lb2 * R(2) * bn;
+        lby += lb2 * R(2) * by;
+        lbz += lb2 * R(2) * bz;
+        R* o = lst[k];
+        o[0] += lr;
+        o[1] += lu;
+        o[2] += lv;
+        o[3] += lw;
+        o[4] += lp;
+        o[5] += lby;
+        o[6] += lbz;
+    }
+}
+
 // d emf2d: lE -> cotangents of the four corner states (rho, p, ua, ub, Ba, Bb, Be each)
 template <typename R>
 MHD_HD void emf2d_vjp(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>& NW, const Corner<R>& NE, R gamma,

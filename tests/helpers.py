@@ -31,22 +31,23 @@ def rounded(flat, dtype):
     return np.asarray(flat, dtype=np.float64)
 
 
-def oracle_bunch(geom, gamma, courant=0.8, limiter=0, dtype=torch.float64):
-    return O.Bunch(geom, gamma, courant=courant, limiter=limiter, eps=O.HLLD_EPS[4 if dtype == torch.float32 else 8])
+def oracle_bunch(geom, gamma, courant=0.8, limiter=0, dtype=torch.float64, riemann=0):
+    return O.Bunch(geom, gamma, courant=courant, limiter=limiter, eps=O.HLLD_EPS[4 if dtype == torch.float32 else 8],
+                   riemann=riemann)
 
 
-def oracle_steps(geom, flat, gamma, dts, limiter=0, dtype=torch.float64):
+def oracle_steps(geom, flat, gamma, dts, limiter=0, dtype=torch.float64, riemann=0):
     """Oracle: fill + step for each dt in dts; returns the final flat buffer."""
-    B = oracle_bunch(geom, gamma, limiter=limiter, dtype=dtype)
+    B = oracle_bunch(geom, gamma, limiter=limiter, dtype=dtype, riemann=riemann)
     P = B.split(flat)
     for dt in dts:
         P = B.step(P, dt)
     return B.join(P)
 
 
-def gpu_bunch(geom, flat, gamma, dtype, courant=0.8, limiter=0, mode=None, config=-1):
+def gpu_bunch(geom, flat, gamma, dtype, courant=0.8, limiter=0, mode=None, config=-1, riemann=0):
     from paper_2508_09568_gb300.bunch import MHDBunch
-    b = MHDBunch(geom, dtype=dtype, gamma=gamma, courant=courant, limiter=limiter)
+    b = MHDBunch(geom, dtype=dtype, gamma=gamma, courant=courant, limiter=limiter, riemann=riemann)
     if mode is not None:
         b.set_mode(mode, config)
     b.upload(flat)

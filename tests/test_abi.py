@@ -61,6 +61,7 @@ def test_argument_validation_before_any_device_call(lib):
     assert lib.mhd_bunch_step(None, 0.1) == capi.MHD_EINVAL
     assert lib.mhd_bunch_step_adjoint(None, 0.1, None, None, None) == capi.MHD_EINVAL
     lib.mhd_bunch_destroy(None)   # no-op
+    assert lib.mhd_bunch_set_riemann(None, 0) == capi.MHD_EINVAL
     r = ct.c_double()
     assert lib.mhd_probe_fma_rate(2, None, ct.byref(r)) == capi.MHD_EINVAL           # real_bytes
     assert lib.mhd_probe_fma_rate(4, None, None) == capi.MHD_EINVAL                   # no output

@@ -43,6 +43,25 @@ def test_one_step_matches_oracle(case, dtype):
     assert code == 0, msg
 
 
+@pytest.mark.parametrize("case", list(_cases()))
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
+def test_one_step_hll_matches_oracle(case, dtype):
+    """The HLL face-flux variant (the paper's mockup solver) against the oracle's HLL step."""
+    geom, U, meta = _cases()[case]()
+    flat = rounded(W.to_patches(U, geom), dtype)
+    ob = oracle_bunch(geom, meta["gamma"], dtype=dtype)
+    dt = ob.cfl_dt(ob.fill_guards(ob.split(flat)))
+    ref = interior_global(oracle_steps(geom, flat, meta["gamma"], [dt], dtype=dtype, riemann=capi.MHD_RIEMANN_HLL),
+                          geom)
+    b = gpu_bunch(geom, flat, meta["gamma"], dtype, riemann=capi.MHD_RIEMANN_HLL)
+    got = interior_global(gpu_steps(b, [dt]), geom)
+    err = rel_l1(got, ref)
+    assert np.all(err <= TOL_STEP[dtype]), err
+    # and it is a different scheme: HLLD's result differs
+    b2 = gpu_bunch(geom, flat, meta["gamma"], dtype)
+    assert not np.array_equal(interior_global(gpu_steps(b2, [dt]), geom), got)
+
+
 @pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
 def test_several_steps_per_step_tolerance(dtype):
     """Five steps, each compared from the same starting state on both sides."""
