@@ -251,6 +251,12 @@ def adjoint_leg(dev, dtype, rollout_steps=200, ckpt=10, reps=5):
                         "ratio": (t2 - t1) / (t1 - t0)}}
 
 
+def workload_name(args, npatch):
+    return (f"3D periodic MHD turbulence box {args.ncell}^3 as {npatch} patches of {args.patch}^3 (guard 3), "
+            f"seeded solenoidal v, rms Mach 1, {args.dtype}; step = fill + CFL dt + persistent fused update "
+            "in a CUDA graph")
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -267,7 +273,9 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps,
             "warmup": warm, "ms_per_step": 1e3 * el / max(steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D MHD turbulence box sample: 8 patches of 32^3 per step (FP64 oracle on host)"},
+            "config": {"workload": workload_name(args, (args.ncell // args.patch) ** 3),
+                       "sample": "each step: 8 patches of 32^3 of the same generator (a 64^3 periodic box) "
+                                 "advanced by the FP64 oracle on the host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -415,9 +423,7 @@ def run_ours(args, ws, rank, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": {"workload": f"3D periodic MHD turbulence box {args.ncell}^3 as {geom.npatch} patches of "
-                                  f"{args.patch}^3 (guard 3), seeded solenoidal v, rms Mach 1, {args.dtype}; "
-                                  "step = fill + CFL dt + persistent fused update in a CUDA graph",
+           "config": {"workload": workload_name(args, geom.npatch),
                       "cells": cells, "patches": geom.npatch, "patch": args.patch,
                       "tile": {"x": tile[0], "y": tile[1], "threads": tile[2]},
                       "l2": f"inputs larger than L2 (state {b.nbytes / 1e9:.2f} GB per buffer)",
