@@ -206,6 +206,43 @@ def ragged_leg(dev, steps):
                                 "launches_per_step": geom.npatch + 2}}
 
 
+def async_leg(b, host, geom, spans=4):
+    """Asynchronous per-patch stepping against synchronous stepping over the same time span
+    (spans global CFL steps of the starting state), both from the same state: patch updates,
+    wall time, and the cell-update rate of the asynchronous run."""
+    def load():
+        with torch.cuda.stream(b.stream):
+            b.current().copy_(host, non_blocking=True)
+        b.stream.synchronize()
+    load()
+    b.fill_guards()
+    t_span = spans * b.cfl_dt()
+    # synchronous: fill -> dt -> step until t_span, the last step clipped
+    t, n = 0.0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while t < t_span:
+        b.fill_guards()
+        dt = min(b.cfl_dt(), t_span - t)
+        b.step(dt)
+        t += dt
+        n += 1
+    b.stream.synchronize()
+    ts = time.perf_counter() - t0
+    load()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rounds, updates = b.advance_async(t_span)
+    ta = time.perf_counter() - t0
+    pc = int(np.prod(geom.patch_n[0]))
+    return {"workload": f"the bench box advanced by {spans} global CFL steps of its starting state",
+            "sync": {"steps": n, "patch_updates": n * geom.npatch, "s": ts},
+            "async": {"rounds": rounds, "patch_updates": updates, "s": ta,
+                      "cell_updates_per_s": updates * pc / ta},
+            "update_ratio_async_over_sync": updates / (n * geom.npatch),
+            "time_ratio_async_over_sync": ta / ts}
+
+
 def adjoint_leg(dev, dtype, rollout_steps=200, ckpt=10, reps=5):
     """Adjoint / forward time on the adjoint workload (64^3 = 8 x 32^3, fixed dt): one step
     (fill + update) against one adjoint step, and a checkpointed rollout's backward against
@@ -435,6 +472,7 @@ def run_ours(args, ws, rank, local):
            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
            "setup_s": {"generate": t_gen}}
     if rank == 0 and not args.no_extra:
+        out["async"] = async_leg(b, host, geom)
         out["ragged"] = ragged_leg(dev, max(3, min(args.steps, 10)))
         out["adjoint_forward_ratio"] = {"workload": "64^3 periodic box, 8 patches of 32^3, fixed dt",
                                         "f64": adjoint_leg(dev, torch.float64),

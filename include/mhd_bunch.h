@@ -132,6 +132,28 @@ int mhd_bunch_step(mhd_bunch *b, double dt);
 /* As mhd_bunch_step with dt read on the device from dt_dev (double). */
 int mhd_bunch_step_device_dt(mhd_bunch *b, const void *dt_dev);
 
+/* Asynchronous per-patch time stepping (DISPATCH's patches at their own times, Sec. 2.2,
+ * updated in bunches of the patches that are ready, Sec. 2.4).  Advances every patch by
+ * t_span from the common time of the current state, in rounds.  Each patch keeps two time
+ * slices (the current one and the one before; the two bound buffers hold them, patch by
+ * patch).  A patch is ready when it is short of t_span and no neighbour (a patch owning a
+ * cell of its guard zone) is at an earlier time; every round updates all ready patches as
+ * one bunch:  guard zones filled at each patch's own time (the neighbours' two slices
+ * interpolated linearly in time), the patch's own CFL dt (courant / max rate over its
+ * cells) clipped to what is left of t_span, the update by that dt.  Conservation and
+ * div B hold inside patches; faces shared by patches at different times are updated by
+ * each side with its own fluxes.  Returns the rounds and the patch updates done; after
+ * the call the current buffer holds every patch at the common time + t_span (ghost cells
+ * not meaningful).  max_rounds >= 1; MHD_ESTATE if max_rounds ran out first.  Synchronises
+ * the bound stream every round (the host schedules). */
+int mhd_bunch_advance_async(mhd_bunch *b, double t_span, int max_rounds, int *rounds,
+                            int64_t *patch_updates);
+/* The record of round `round` of the last mhd_bunch_advance_async: its patches (in
+ * ascending order) and the dt each took.  *n receives the count; patches / dts (either may
+ * be NULL) must hold cap >= *n entries. */
+int mhd_bunch_async_round(const mhd_bunch *b, int round, int32_t *patches, double *dts, int cap,
+                          int *n);
+
 /* Launch mode of the update (MHD_MODE_*) and tile configuration index (0..n-1 from
  * mhd_bunch_num_configs; -1 = library default).  Every mode and every configuration
  * computes bitwise the same state. */

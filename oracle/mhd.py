@@ -607,3 +607,113 @@ class Bunch:
             t += dt
             k += 1
         return patches, t, k
+
+
+# ----------------------------------------------------------------------------------------
+# Asynchronous per-patch stepping (DISPATCH's patches at their own times, Sec. 2.2, updated
+# in bunches of the ready ones, Sec. 2.4).  Readings: each patch keeps two time slices; a
+# patch is ready when it is short of the target time and no neighbour (a patch owning a cell
+# of its guard zone) is at an earlier time; its guard values are the neighbours' two slices
+# interpolated linearly in time to its own time; it steps by its own CFL dt clipped to the
+# target time.
+# ----------------------------------------------------------------------------------------
+
+def owner_map(geom):
+    """Patch index of every box cell (Nz, Ny, Nx)."""
+    own = np.full((int(geom.domain[2]), int(geom.domain[1]), int(geom.domain[0])), -1, dtype=np.int64)
+    for p in range(geom.npatch):
+        o, n = geom.origin[p], geom.patch_n[p]
+        own[o[2]:o[2] + n[2], o[1]:o[1] + n[1], o[0]:o[0] + n[0]] = p
+    return own
+
+
+def _window_index(geom, p):
+    """Box indices (iz, iy, ix) covered by padded patch p (wrap / clamp by the boundary kinds)."""
+    idx = []
+    for d in range(3):
+        r = torch.arange(int(geom.patch_n[p][d]) + 2 * int(geom.gvec[d])) + int(geom.origin[p][d]) - int(geom.gvec[d])
+        idx.append(_wrap(r, int(geom.domain[d]), int(geom.bc[d][0]), int(geom.bc[d][1])).numpy())
+    return idx[2], idx[1], idx[0]
+
+
+def neighbours(geom):
+    """For each patch the set of other patches that own a cell of its guard zone."""
+    own = owner_map(geom)
+    out = []
+    for p in range(geom.npatch):
+        iz, iy, ix = _window_index(geom, p)
+        covered = own[np.ix_(iz, iy, ix)]
+        out.append(set(int(q) for q in np.unique(covered)) - {p})
+    return out
+
+
+def fill_guards_at(cur, old, t_cur, t_old, geom, p):
+    """Padded patch p with every guard cell at time t_cur[p]: the box cell's patch q gives
+    old_q + w (cur_q - old_q), w = (t_cur[p] - t_old[q]) / (t_cur[q] - t_old[q]) (the current
+    slice when w >= 1 or the two slice times are equal, the previous one when w <= 0)."""
+    blended = []
+    for q in range(geom.npatch):
+        den = t_cur[q] - t_old[q]
+        w = (t_cur[p] - t_old[q]) / den if den > 0 else 1.0
+        if w >= 1.0:
+            blended.append(cur[q])
+        elif w <= 0.0:
+            blended.append(old[q])
+        else:
+            blended.append(old[q] + w * (cur[q] - old[q]))
+    G = assemble(blended, geom.patch_n, geom.origin, geom.gvec, geom.domain)
+    return window(G, geom.origin[p], geom.patch_n[p], geom.gvec, geom.domain, geom.bc)
+
+
+class AsyncBunch:
+    """Asynchronous stepping of a bunch (FP64), for checking a recorded schedule."""
+
+    def __init__(self, geom, gamma, courant=0.8, limiter=LIMITER_MINMOD, eps=HLLD_EPS[8], riemann=RIEMANN_HLLD):
+        self.geom = geom
+        self.gamma, self.courant = float(gamma), float(courant)
+        self.limiter, self.eps, self.riemann = int(limiter), float(eps), int(riemann)
+        self.nbrs = neighbours(geom)
+
+    def ready(self, t_cur, t_span):
+        return [p for p in range(self.geom.npatch)
+                if t_cur[p] < t_span and all(t_cur[q] >= t_cur[p] for q in self.nbrs[p])]
+
+    def local_dt(self, filled, p):
+        g, n = self.geom.gvec, self.geom.patch_n[p]
+        r = cfl_rate(filled[None], self.geom.active, self.geom.dx, self.gamma)[0]
+        r = r[g[2]:g[2] + n[2], g[1]:g[1] + n[1], g[0]:g[0] + n[0]]
+        return float(self.courant / r.max())
+
+    def replay(self, patches, rounds, t_span):
+        """Apply a recorded schedule [(patches, dts), ...] to the list of padded patches.
+
+        Returns (final patches, the ready set the rule gives before each round, the local
+        CFL dt of each listed patch clipped to t_span, final times)."""
+        geom = self.geom
+        P = geom.npatch
+        cur = [u.clone() for u in patches]
+        old = [u.clone() for u in patches]
+        t_cur, t_old = [0.0] * P, [0.0] * P
+        ready_sets, local_dts = [], []
+        for plist, dts in rounds:
+            ready_sets.append(self.ready(t_cur, t_span))
+            filled = {int(p): fill_guards_at(cur, old, t_cur, t_old, geom, int(p)) for p in plist}
+            ldt = []
+            for p in plist:
+                p = int(p)
+                ldt.append(min(self.local_dt(filled[p], p), t_span - t_cur[p]))
+            local_dts.append(ldt)
+            new = {}
+            for p, dt in zip(plist, dts):
+                p = int(p)
+                n = geom.patch_n[p]
+                new[p] = step(filled[p][None], float(dt), geom.active, geom.dx, self.gamma, self.limiter, self.eps,
+                              gvec=geom.gvec, n=n, riemann=self.riemann)[0]
+            for p, dt in zip(plist, dts):
+                p = int(p)
+                old[p] = cur[p]
+                cur[p] = new[p]
+                t_old[p] = t_cur[p]
+                t_cur[p] = t_cur[p] + float(dt) if float(dt) < t_span - t_cur[p] else t_span
+            # (a clipped last step lands exactly on t_span)
+        return cur, ready_sets, local_dts, t_cur

@@ -149,6 +149,27 @@ class MHDBunch:
                                                        ct.byref(t)))
         return t.value
 
+    def advance_async(self, t_span: float, max_rounds: int = 100000):
+        """Asynchronous per-patch stepping by t_span (mhd_bunch_advance_async); returns
+        (rounds, patch_updates)."""
+        r = ct.c_int()
+        u = ct.c_int64()
+        capi.check(self.lib.mhd_bunch_advance_async(self.h, float(t_span), int(max_rounds), ct.byref(r), ct.byref(u)))
+        return r.value, u.value
+
+    def async_rounds(self, nrounds: int):
+        """[(patches int32, dts float64)] of the last advance_async, one entry per round."""
+        out = []
+        for k in range(nrounds):
+            n = ct.c_int()
+            capi.check(self.lib.mhd_bunch_async_round(self.h, k, None, None, 0, ct.byref(n)))
+            pp = np.zeros(n.value, dtype=np.int32)
+            dd = np.zeros(n.value, dtype=np.float64)
+            capi.check(self.lib.mhd_bunch_async_round(self.h, k, pp.ctypes.data_as(capi.I32P),
+                                                      dd.ctypes.data_as(capi.DP), n.value, ct.byref(n)))
+            out.append((pp, dd))
+        return out
+
     def step_adjoint(self, dt: float, U_n: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor):
         for t in (U_n, lam_next, lam):
             assert t.is_cuda and t.dtype == self.dtype and t.numel() * self.rb == self.nbytes

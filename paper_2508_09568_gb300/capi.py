@@ -52,6 +52,8 @@ SIGNATURES = {
     "mhd_bunch_graph_launch": (I, [P]),
     "mhd_bunch_advance_host": (I, [P, P, I, DP]),
     "mhd_bunch_advance_streamed": (I, [P, P, I, I, DP]),
+    "mhd_bunch_advance_async": (I, [P, D, I, ct.POINTER(I), I64P]),
+    "mhd_bunch_async_round": (I, [P, I, I32P, DP, I, ct.POINTER(I)]),
     "mhd_bunch_step_adjoint": (I, [P, D, P, P, P]),
     "mhd_bunch_get_error": (I, [P, ct.POINTER(I), ct.c_char_p, ct.c_size_t]),
     "mhd_bunch_launch_count": (I, [P, I64P]),

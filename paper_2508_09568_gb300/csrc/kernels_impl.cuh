@@ -13,6 +13,8 @@ static StepArgs<R> to_args(const StepHostArgs& h) {
     StepArgs<R> a;
     a.U = static_cast<const R*>(h.U);
     a.Unew = static_cast<R*>(h.Unew);
+    a.slice = h.slice;
+    a.dt_patch = h.dt_patch;
     a.patches = h.patches;
     a.tiles = h.tiles;
     a.ntiles = h.ntiles;
@@ -34,16 +36,23 @@ struct StepInst {
     using C = StepCfg<R, NDIM, TX, TY, NT>;
     static_assert(C::SMEM_BYTES * MINB <= 227 * 1024, "tile too large for shared memory");
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH>,
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM_BYTES);
     }
     static cudaError_t occupancy(int* blocks) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH>, NT,
-                                                             C::SMEM_BYTES);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH, false>,
+                                                             NT, C::SMEM_BYTES);
     }
+    // asynchronous stepping (a.slice set) runs its own instantiation
     static cudaError_t launch(const void* args, int grid, cudaStream_t s) {
         const StepArgs<R> a = to_args<R>(*static_cast<const StepHostArgs*>(args));
-        step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH><<<grid, NT, C::SMEM_BYTES, s>>>(a);
+        if (a.slice)
+            step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH, true><<<grid, NT, C::SMEM_BYTES, s>>>(a);
+        else
+            step_kernel<R, NDIM, TX, TY, NT, MINB, PREFETCH, false><<<grid, NT, C::SMEM_BYTES, s>>>(a);
         return cudaGetLastError();
     }
     static StepLaunch entry() {
@@ -60,6 +69,29 @@ static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, con
         dim3 grid(8, npatch < 65535 ? npatch : 65535);
         fill_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U), patches, npatch, fg, err);
     }
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_fill_interp(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list,
+                                     int nlist, const int* slice, const double* t_old, const double* t_cur,
+                                     const FillGeom& fg, unsigned* err, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    dim3 grid(8, nlist < 65535 ? nlist : 65535);
+    fill_interp_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U0), static_cast<R*>(U1), patches, npatch, list, nlist,
+                                               slice, t_old, t_cur, fg, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_cfl_patch(const void* U0, const void* U1, const PatchDev* patches, const int* list,
+                                   int nlist, const int* slice, double gamma, double courant, const double dxi[3],
+                                   const int act[3], double* dt_out, unsigned* err, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    const int grid = nlist < 65535 ? nlist : 65535;
+    cfl_patch_kernel<R><<<grid, 256, 0, s>>>(static_cast<const R*>(U0), static_cast<const R*>(U1), patches, list,
+                                             nlist, slice, gamma, courant, dxi[0], dxi[1], dxi[2], act[1], act[2],
+                                             dt_out, err);
     return cudaGetLastError();
 }
 

@@ -185,6 +185,23 @@ struct CflArgs {
     unsigned* err;
 };
 
+// CFL rate of the interior cell c (pointer to its rho) of a patch: sum over active axes of
+// (|u_d| + c_f,d) / dx_d, with the cell-centred field the mean of the cell's two faces
+template <typename R>
+__device__ __forceinline__ R cell_rate(const R* c, int64_t vol, int sy, int sz, bool act1, bool act2, R gamma,
+                                       R gm1, R dxi0, R dxi1, R dxi2) {
+    const R bxc = R(0.5) * (c[5 * vol] + c[5 * vol + 1]);
+    const R byc = act1 ? R(0.5) * (c[6 * vol] + c[6 * vol + sy]) : c[6 * vol];
+    const R bzc = act2 ? R(0.5) * (c[7 * vol] + c[7 * vol + sz]) : c[7 * vol];
+    R q[8];
+    cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
+    const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
+    R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
+    if (act1) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
+    if (act2) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;
+    return rate;
+}
+
 template <typename R>
 __global__ void cfl_kernel(CflArgs<R> a) {
     __shared__ R red[32];
@@ -201,15 +218,7 @@ __global__ void cfl_kernel(CflArgs<R> a) {
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
             const R* c = a.U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
-            const R bxc = R(0.5) * (c[5 * vol] + c[5 * vol + 1]);
-            const R byc = a.act[1] ? R(0.5) * (c[6 * vol] + c[6 * vol + sy]) : c[6 * vol];
-            const R bzc = a.act[2] ? R(0.5) * (c[7 * vol] + c[7 * vol + sz]) : c[7 * vol];
-            R q[8];
-            cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
-            const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
-            R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
-            if (a.act[1]) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
-            if (a.act[2]) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;
+            const R rate = cell_rate(c, vol, sy, sz, a.act[1] != 0, a.act[2] != 0, gamma, gm1, dxi0, dxi1, dxi2);
             if (!isfinite((double)rate)) bad = true;
             else vmax = rate > vmax ? rate : vmax;
         }
@@ -235,6 +244,97 @@ __global__ void cfl_kernel(CflArgs<R> a) {
             *a.dt_out = a.courant / (double)v;
             *a.counter = 0u;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Asynchronous stepping (patches at their own times, two time slices each: the current one
+// in buffer slice[p] of (U0, U1), the previous one in the other).
+// ---------------------------------------------------------------------------------------
+
+// a1 at each listed patch's own time t_cur[p]: a ghost cell takes the value of the box cell
+// it stands for (owner map, wrap / clamp as fill_kernel) interpolated linearly in time
+// between the owner's two slices, w = (t_cur[p] - t_old[q]) / (t_cur[q] - t_old[q]); w >= 1
+// (or equal slice times) takes the current slice exactly, w <= 0 the previous one.
+template <typename R>
+__global__ void fill_interp_kernel(R* __restrict__ U0, R* __restrict__ U1, const PatchDev* __restrict__ patches,
+                                   int npatch, const int* __restrict__ list, int nlist, const int* __restrict__ slice,
+                                   const double* __restrict__ t_old, const double* __restrict__ t_cur, FillGeom fg,
+                                   unsigned* err) {
+    for (int L = blockIdx.y; L < nlist; L += gridDim.y) {
+        const int p = list[L];
+        const PatchDev pt = patches[p];
+        const int ng = ghost_count(pt);
+        const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
+        R* Up = (slice[p] ? U1 : U0) + pt.off;
+        const double tp = t_cur[p];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
+            int x, y, z;
+            ghost_coord(pt, k, x, y, z);
+            const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
+            const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
+            const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
+            const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
+            if (ow < 0 || ow >= npatch) {
+                atomicOr(err, ERR_BOUNDS);
+                continue;
+            }
+            const PatchDev src = patches[ow];
+            const int64_t so = src.off + ((int64_t)(gzg - src.oz + src.gz) * src.Y + (gyg - src.oy + src.gy)) * src.X +
+                               (gxg - src.ox + src.gx);
+            const int64_t svol = (int64_t)src.X * src.Y * src.Z;
+            const R* cur = (slice[ow] ? U1 : U0) + so;
+            const R* old = (slice[ow] ? U0 : U1) + so;
+            const double den = t_cur[ow] - t_old[ow];
+            const double w = den > 0.0 ? (tp - t_old[ow]) / den : 1.0;
+            R* d = Up + ((int64_t)z * pt.Y + y) * pt.X + x;
+            if (w >= 1.0) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) d[v * vol] = cur[v * svol];
+            } else if (w <= 0.0) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) d[v * vol] = old[v * svol];
+            } else {
+                const R wr = R(w);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const R o = old[v * svol];
+                    d[v * vol] = o + wr * (cur[v * svol] - o);
+                }
+            }
+        }
+    }
+}
+
+// a2 per listed patch: dt_out[p] = courant / (max CFL rate over the patch's interior cells)
+// of its current slice (one block per listed patch).  Non-finite rates set ERR_PHYS.
+template <typename R>
+__global__ void cfl_patch_kernel(const R* __restrict__ U0, const R* __restrict__ U1,
+                                 const PatchDev* __restrict__ patches, const int* __restrict__ list, int nlist,
+                                 const int* __restrict__ slice, double gamma_d, double courant, double dxi0_d,
+                                 double dxi1_d, double dxi2_d, int act1, int act2, double* dt_out, unsigned* err) {
+    __shared__ R red[32];
+    const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
+    const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
+    for (int L = blockIdx.x; L < nlist; L += gridDim.x) {
+        const int p = list[L];
+        const PatchDev pt = patches[p];
+        const int n = pt.nx * pt.ny * pt.nz;
+        const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
+        const R* base = (slice[p] ? U1 : U0) + pt.off;
+        R vmax = R(0);
+        bool bad = false;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
+            const R* c = base + ((int64_t)z * pt.Y + y) * pt.X + x;
+            const R rate = cell_rate(c, vol, pt.X, pt.X * pt.Y, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
+            if (!isfinite((double)rate)) bad = true;
+            else vmax = rate > vmax ? rate : vmax;
+        }
+        if (bad) atomicOr(err, ERR_PHYS);
+        const R bm = block_max(vmax, red);
+        if (threadIdx.x == 0) dt_out[p] = courant / (double)bm;
+        __syncthreads();
     }
 }
 

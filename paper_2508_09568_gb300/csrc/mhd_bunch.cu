@@ -72,6 +72,7 @@ struct mhd_bunch {
         int4* d_nat = nullptr;
         int4* d_lpt = nullptr;
         int n = 0;
+        std::vector<int4> nat_h;             // host copy of the natural order
         std::vector<int> first, count;   // per patch, in natural order
     };
     std::vector<Tiles> tiles;
@@ -90,6 +91,20 @@ struct mhd_bunch {
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;                         // index of the buffer holding U^n
     cudaStream_t stream = nullptr;
+    // asynchronous stepping: neighbour lists (owners of each patch's guard zone), per-patch
+    // times and slices, device mirrors, and the record of the last run's rounds
+    std::vector<std::vector<int>> nbrs;
+    std::vector<int> owner_h;
+    int64_t ob_bs[3] = {1, 1, 1}, ob_M[3] = {1, 1, 1};
+    int* d_slice = nullptr;
+    double* d_told = nullptr;
+    double* d_tcur = nullptr;
+    double* d_dtp = nullptr;
+    int* d_list = nullptr;
+    int4* d_atiles = nullptr;
+    int atiles_cap = 0;
+    std::vector<std::vector<int>> log_patches;
+    std::vector<std::vector<double>> log_dts;
     // host-streamed advance: library-owned copy streams and per-chunk events
     cudaStream_t s_in = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_step, ev_out;
@@ -241,6 +256,7 @@ int build_tiles(mhd_bunch* b) {
             T.count[p] = (int)nat.size() - T.first[p];
         }
         std::vector<int4> lpt = nat;
+        T.nat_h = nat;
         std::stable_sort(lpt.begin(), lpt.end(), [](const int4& a, const int4& c) { return a.w > c.w; });
         T.n = (int)nat.size();
         CK(cudaMalloc(&T.d_nat, sizeof(int4) * T.n));
@@ -255,6 +271,8 @@ StepHostArgs step_args(mhd_bunch* b, const double* dt_ptr, double dt_val) {
     StepHostArgs a;
     a.U = b->buf[b->cur];
     a.Unew = b->buf[1 - b->cur];
+    a.slice = nullptr;
+    a.dt_patch = nullptr;
     a.patches = b->d_patches;
     a.tiles = nullptr;
     a.ntiles = 0;
@@ -403,6 +421,62 @@ int ensure_stream_pipeline(mhd_bunch* b, int nchunks) {
     return MHD_OK;
 }
 
+// Neighbours of every patch for asynchronous stepping: the patches other than p that own a
+// cell of p's guard zone (wrap / clamp as the guard fill).  Axes in the guard direction are
+// walked cell by cell, the others by owner-map block.
+void build_neighbours(mhd_bunch* b) {
+    b->nbrs.assign(b->npatch, {});
+    const int g = b->guard;
+    for (int p = 0; p < b->npatch; ++p) {
+        std::vector<int>& out = b->nbrs[p];
+        for (int sz = -1; sz <= 1; ++sz)
+            for (int sy = -1; sy <= 1; ++sy)
+                for (int sx = -1; sx <= 1; ++sx) {
+                    const int s3[3] = {sx, sy, sz};
+                    if (!sx && !sy && !sz) continue;
+                    int64_t lo[3], hi[3], st[3];
+                    bool ok = true;
+                    for (int d = 0; d < 3; ++d) {
+                        const int64_t o = b->origin[3 * p + d], n = b->pn[3 * p + d];
+                        if (n == 1 && s3[d] != 0) ok = false;
+                        if (s3[d] < 0) { lo[d] = o - g; hi[d] = o; st[d] = 1; }
+                        else if (s3[d] > 0) { lo[d] = o + n; hi[d] = o + n + g; st[d] = 1; }
+                        else { lo[d] = o; hi[d] = o + n; st[d] = b->ob_bs[d]; }
+                    }
+                    if (!ok) continue;
+                    for (int64_t z = lo[2]; z < hi[2]; z += st[2])
+                        for (int64_t y = lo[1]; y < hi[1]; y += st[1])
+                            for (int64_t x = lo[0]; x < hi[0]; x += st[0]) {
+                                const int64_t c[3] = {x, y, z};
+                                int64_t w[3];
+                                for (int d = 0; d < 3; ++d) {
+                                    const int64_t N = b->domain[d];
+                                    if (c[d] < 0) w[d] = b->bc[2 * d] == MHD_BC_PERIODIC ? ((c[d] % N) + N) % N : 0;
+                                    else if (c[d] >= N) w[d] = b->bc[2 * d + 1] == MHD_BC_PERIODIC ? c[d] % N : N - 1;
+                                    else w[d] = c[d];
+                                }
+                                const int q = b->owner_h[(size_t)(((w[2] / b->ob_bs[2]) * b->ob_M[1] + w[1] / b->ob_bs[1]) *
+                                                                  b->ob_M[0] + w[0] / b->ob_bs[0])];
+                                if (q != p && std::find(out.begin(), out.end(), q) == out.end()) out.push_back(q);
+                            }
+                }
+        std::sort(out.begin(), out.end());
+    }
+}
+
+int ensure_async(mhd_bunch* b) {
+    if (b->nbrs.empty()) build_neighbours(b);
+    const size_t P = (size_t)b->npatch;
+    if (!b->d_slice) {
+        CK(cudaMalloc(&b->d_slice, sizeof(int) * P));
+        CK(cudaMalloc(&b->d_told, sizeof(double) * P));
+        CK(cudaMalloc(&b->d_tcur, sizeof(double) * P));
+        CK(cudaMalloc(&b->d_dtp, sizeof(double) * P));
+        CK(cudaMalloc(&b->d_list, sizeof(int) * P));
+    }
+    return MHD_OK;
+}
+
 int read_error(mhd_bunch* b, int* code, char* msg, size_t len) {
     unsigned h = 0;
     CK(cudaMemcpyAsync(&h, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
@@ -492,6 +566,12 @@ int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patc
     for (int o : owner)
         if (o < 0) return fail(MHD_EINVAL, "patches do not cover the box");
     release_graph(b);
+    b->owner_h = owner;
+    for (int d = 0; d < 3; ++d) {
+        b->ob_bs[d] = bs[d];
+        b->ob_M[d] = M[d];
+    }
+    b->nbrs.clear();
     cudaFree(b->d_owner);
     b->d_owner = nullptr;
     CK(cudaMalloc(&b->d_owner, sizeof(int) * owner.size()));
@@ -904,6 +984,142 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
     return code;
 }
 
+int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* rounds, int64_t* patch_updates) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!(t_span >= 0) || !std::isfinite(t_span) || max_rounds < 1) return fail(MHD_EINVAL, "bad argument");
+    if (b->cfg_index.empty()) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
+    rc = ensure_async(b);
+    if (rc) return rc;
+    const int P = b->npatch;
+    const int A = b->cur;
+    std::vector<double> t_old(P, 0.0), t_cur(P, 0.0), dtp(P, 0.0);
+    std::vector<int> slice(P, 0);
+    double dxi[3];
+    int act[3];
+    for (int d = 0; d < 3; ++d) {
+        dxi[d] = 1.0 / b->dx[d];
+        act[d] = active(b, d);
+    }
+    const int k = b->config < 0 ? default_config(b) : b->config;
+    const StepLaunch& L = step_cfg(b, k);
+    const auto& T = b->tiles[k];
+    int occ = 1;
+    CK(L.occupancy(&occ));
+    occ = std::max(occ, 1);
+    b->log_patches.clear();
+    b->log_dts.clear();
+    int64_t updates = 0;
+    int r = 0;
+    for (; r < max_rounds; ++r) {
+        // ready: not yet at t_span and not ahead of any neighbour
+        std::vector<int> list;
+        for (int p = 0; p < P; ++p) {
+            if (!(t_cur[p] < t_span)) continue;
+            bool ok = true;
+            for (int q : b->nbrs[p])
+                if (t_cur[q] < t_cur[p]) { ok = false; break; }
+            if (ok) list.push_back(p);
+        }
+        if (list.empty()) break;
+        const int n = (int)list.size();
+        CK(cudaMemcpyAsync(b->d_list, list.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_slice, slice.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_told, t_old.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_tcur, t_cur.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
+        // guard zones at each patch's own time, then its own CFL dt
+        CK(b->K->fill_interp(b->buf[A], b->buf[1 - A], b->d_patches, P, b->d_list, n, b->d_slice, b->d_told,
+                             b->d_tcur, b->fg, b->d_err, b->stream));
+        CK(b->K->cfl_patch(b->buf[A], b->buf[1 - A], b->d_patches, b->d_list, n, b->d_slice, b->gamma, b->courant,
+                           dxi, act, b->d_dtp, b->d_err, b->stream));
+        b->launches += 2;
+        CK(cudaMemcpyAsync(dtp.data(), b->d_dtp, sizeof(double) * P, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        std::vector<double> used(n);
+        std::vector<bool> last(n, false);
+        for (int i = 0; i < n; ++i) {
+            const int p = list[i];
+            const double rem = t_span - t_cur[p];
+            if (!(dtp[p] > 0) || !std::isfinite(dtp[p])) {
+                int code = 0;
+                read_error(b, &code, nullptr, 0);
+                return code ? code : fail(MHD_EPHYS, "non-finite local time step");
+            }
+            if (dtp[p] >= rem) {
+                dtp[p] = rem;
+                last[i] = true;
+            }
+            used[i] = dtp[p];
+        }
+        CK(cudaMemcpyAsync(b->d_dtp, dtp.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
+        // the update of the listed patches, each by its own dt, current slice -> the other
+        std::vector<int4> tl;   // the listed patches' tiles (contiguous per patch in the natural order)
+        for (int p : list)
+            tl.insert(tl.end(), T.nat_h.begin() + T.first[p], T.nat_h.begin() + T.first[p] + T.count[p]);
+        if ((int)tl.size() > b->atiles_cap) {
+            cudaFree(b->d_atiles);
+            b->d_atiles = nullptr;
+            CK(cudaMalloc(&b->d_atiles, sizeof(int4) * T.n));
+            b->atiles_cap = T.n;
+        }
+        CK(cudaMemcpyAsync(b->d_atiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, b->stream));
+        StepHostArgs a = step_args(b, nullptr, 0.0);
+        a.U = b->buf[A];
+        a.Unew = b->buf[1 - A];
+        a.slice = b->d_slice;
+        a.dt_patch = b->d_dtp;
+        a.tiles = b->d_atiles;
+        a.ntiles = (int)tl.size();
+        a.dynamic = 1;
+        CK(L.launch(&a, std::min((int)tl.size(), b->nsm * occ), b->stream));
+        b->launches++;
+        for (int i = 0; i < n; ++i) {
+            const int p = list[i];
+            t_old[p] = t_cur[p];
+            t_cur[p] = last[i] ? t_span : t_cur[p] + used[i];
+            slice[p] ^= 1;
+        }
+        updates += n;
+        b->log_patches.push_back(list);
+        b->log_dts.push_back(used);
+    }
+    // gather: every patch's final slice into the current buffer (runs of consecutive patches)
+    for (int p = 0; p < P;) {
+        if (!slice[p]) { ++p; continue; }
+        int q = p;
+        while (q + 1 < P && slice[q + 1]) ++q;
+        const size_t lo = (size_t)b->offs[p] * b->rb;
+        const size_t hi = q + 1 < P ? (size_t)b->offs[q + 1] * b->rb : b->state_bytes;
+        CK(cudaMemcpyAsync(static_cast<char*>(b->buf[A]) + lo, static_cast<char*>(b->buf[1 - A]) + lo, hi - lo,
+                           cudaMemcpyDeviceToDevice, b->stream));
+        p = q + 1;
+    }
+    if (rounds) *rounds = r;
+    if (patch_updates) *patch_updates = updates;
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    if (code) return code;
+    for (int p = 0; p < P; ++p)
+        if (t_cur[p] < t_span) return fail(MHD_ESTATE, "max_rounds reached before every patch arrived at t_span");
+    return MHD_OK;
+}
+
+int mhd_bunch_async_round(const mhd_bunch* b, int round, int32_t* patches, double* dts, int cap, int* n) {
+    if (!b || !n) return fail(MHD_EINVAL, "NULL argument");
+    if (round < 0 || round >= (int)b->log_patches.size()) return fail(MHD_EINVAL, "no such round");
+    const auto& lp = b->log_patches[round];
+    *n = (int)lp.size();
+    if (patches || dts) {
+        if (cap < *n) return fail(MHD_EINVAL, "cap smaller than the round's patch count");
+        for (int i = 0; i < *n; ++i) {
+            if (patches) patches[i] = lp[i];
+            if (dts) dts[i] = b->log_dts[round][i];
+        }
+    }
+    return MHD_OK;
+}
+
 int mhd_bunch_get_error(mhd_bunch* b, int* code, char* msg, size_t len) {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     return read_error(b, code, msg, len);
@@ -923,6 +1139,12 @@ void mhd_bunch_destroy(mhd_bunch* b) {
         for (cudaEvent_t e : *v) cudaEventDestroy(e);
     if (b->s_in) cudaStreamDestroy(b->s_in);
     if (b->s_out) cudaStreamDestroy(b->s_out);
+    cudaFree(b->d_slice);
+    cudaFree(b->d_told);
+    cudaFree(b->d_tcur);
+    cudaFree(b->d_dtp);
+    cudaFree(b->d_list);
+    cudaFree(b->d_atiles);
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);

@@ -50,6 +50,14 @@ struct PrecisionKernels {
     // G must be zeroed before the call
     cudaError_t (*adjoint)(const AdjHostArgs& a, const FillGeom& fg, unsigned* err, cudaStream_t s, int* nlaunch);
     int adj_fields;      // work fields per cell in F and in G
+    // asynchronous stepping: guard fill of the listed patches at their own times, and
+    // their own CFL dt (dt_out indexed by patch)
+    cudaError_t (*fill_interp)(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list, int nlist,
+                               const int* slice, const double* t_old, const double* t_cur, const FillGeom& fg,
+                               unsigned* err, cudaStream_t s);
+    cudaError_t (*cfl_patch)(const void* U0, const void* U1, const PatchDev* patches, const int* list, int nlist,
+                             const int* slice, double gamma, double courant, const double dxi[3], const int act[3],
+                             double* dt_out, unsigned* err, cudaStream_t s);
 };
 
 const PrecisionKernels& kernels_f32();
@@ -59,6 +67,8 @@ const PrecisionKernels& kernels_f64();
 struct StepHostArgs {
     const void* U;
     void* Unew;
+    const int* slice;        // asynchronous stepping (else null): current slice per patch
+    const double* dt_patch;  // asynchronous stepping (else null): dt per patch
     const PatchDev* patches;
     const int4* tiles;
     int ntiles;

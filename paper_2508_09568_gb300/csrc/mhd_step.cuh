@@ -373,6 +373,11 @@ template <typename R>
 struct StepArgs {
     const R* __restrict__ U;
     R* __restrict__ Unew;
+    // asynchronous stepping (both null otherwise): patch p reads its current time slice
+    // from buffer slice[p] (U when 0, Unew when 1) and writes the new one into the other
+    // buffer, advancing by its own dt_patch[p]
+    const int* __restrict__ slice;
+    const double* __restrict__ dt_patch;
     const PatchDev* __restrict__ patches;
     const int4* __restrict__ tiles;
     int ntiles;
@@ -446,7 +451,9 @@ __device__ __forceinline__ void stage_update(const StepSmem<R, C>& S, const R* _
 // PREFETCH (3D): the raw plane m+1 is copied with cp.async into the W-ring slot of plane
 // c-1 (free once plane c is prepared) while the flux stage of plane c runs, instead of
 // being loaded at the start of the next iteration.
-template <typename R, int NDIM, int TX, int TY, int NT, int MINB, bool PREFETCH>
+// ASYNC: asynchronous stepping (a.slice, a.dt_patch): per-tile slice choice and dt; a
+// separate instantiation so that the synchronous step keeps its kernel-wide constants.
+template <typename R, int NDIM, int TX, int TY, int NT, int MINB, bool PREFETCH, bool ASYNC>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     using C = StepCfg<R, NDIM, TX, TY, NT>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -459,11 +466,11 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     __shared__ R bznext[C::LSZ];
     __shared__ int s_tile;
 
-    const double dtd = a.dt_ptr ? *a.dt_ptr : a.dt_val;
-    const R hdt = R(0.5 * dtd);
+    const double dt0 = a.dt_ptr ? *a.dt_ptr : a.dt_val;
     const R gamma = R(a.gamma), gm1 = R(a.gamma - 1.0), gm1i = R(1.0 / (a.gamma - 1.0));
     const R eps = R(a.eps);
-    const R dtdx0 = R(dtd * a.dxi[0]), dtdx1 = R(dtd * a.dxi[1]), dtdx2 = R(dtd * a.dxi[2]);
+    R hdt = R(0.5 * dt0);
+    R dtdx0 = R(dt0 * a.dxi[0]), dtdx1 = R(dt0 * a.dxi[1]), dtdx2 = R(dt0 * a.dxi[2]);
 
     int t;
     if (a.dynamic) {
@@ -476,6 +483,19 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     while (t < a.ntiles) {
         const int4 tl = a.tiles[t];
         const PatchDev pt = a.patches[tl.x];
+        const R* __restrict__ Uc = a.U;
+        R* __restrict__ Un = a.Unew;
+        if constexpr (ASYNC) {
+            const double dtd = a.dt_patch[tl.x];
+            hdt = R(0.5 * dtd);
+            dtdx0 = R(dtd * a.dxi[0]);
+            dtdx1 = R(dtd * a.dxi[1]);
+            dtdx2 = R(dtd * a.dxi[2]);
+            if (a.slice[tl.x]) {
+                Uc = a.Unew;
+                Un = const_cast<R*>(a.U);
+            }
+        }
         const int x0 = tl.y, y0 = tl.z;
         const int wx = min(C::TX, pt.nx - x0), wy = C::AY ? min(C::TY, pt.ny - y0) : 1;
         const int nz = C::AZ ? pt.nz : 1;
@@ -500,9 +520,9 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
             // with the prefetch, plane m was issued in the previous iteration's flux stage
             R* Wm_slot = S.W(C::AZ ? (m + 3) % 3 : 0);
             if ((!PF || s == 0) && (!C::AZ || m <= nz + 1))
-                stage_load<R, C, PF>(a.U, pt, x0, y0, m, Wm_slot, bznext);
+                stage_load<R, C, PF>(Uc, pt, x0, y0, m, Wm_slot, bznext);
             if (C::AZ && s >= 5)
-                stage_update<R, C>(S, a.U, a.Unew, pt, x0, y0, s - 5, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
+                stage_update<R, C>(S, Uc, Un, pt, x0, y0, s - 5, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
             if (PF) cp_async_wait_all();
             __syncthreads();
             if (C::AZ && m > nz + 1) break;      // the last update is done
@@ -523,7 +543,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
             }
             __syncthreads();
             // ---- prefetch plane m+1 into the slot of plane c-1 (read by nobody from here on)
-            if (PF && m + 1 <= nz + 1) stage_load<R, C, true>(a.U, pt, x0, y0, m + 1, S.W((m + 4) % 3), bznext);
+            if (PF && m + 1 <= nz + 1) stage_load<R, C, true>(Uc, pt, x0, y0, m + 1, S.W((m + 4) % 3), bznext);
             // ---- fluxes of plane c and between planes c-1 and c
             if (c >= 0) {
                 const R* P0 = S.P(C::AZ ? (c + 2) & 1 : 0);
@@ -644,7 +664,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
             }
             __syncthreads();
             if (!C::AZ) {
-                stage_update<R, C>(S, a.U, a.Unew, pt, x0, y0, 0, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
+                stage_update<R, C>(S, Uc, Un, pt, x0, y0, 0, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
             }
         }
         // next tile
