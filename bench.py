@@ -4,8 +4,8 @@
 Workload (the 3D headline configuration): a 512^3 periodic MHD turbulence-like box as
 4096 patches of 32^3 cells (guard 3), rho = 1, p = 1, gamma = 5/3, B = (0.1, 0, 0),
 seeded solenoidal velocity with E(k) ~ k^-2 over 1 <= |k| <= 8 and rms Mach 1, FP32.
-One step = guard fill + CFL dt on the device + fused update (persistent kernel), the
-sequence captured in a CUDA graph.  Metric: 3D MHD cell-updates per second.
+One step = guard fill + CFL dt on the device (one pass) + fused update (persistent
+kernel), the sequence captured in a CUDA graph.  Metric: 3D MHD cell-updates per second.
 
 Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent replica of
 the box on its own GPU (the box is not split across GPUs: replicas only), and value is
@@ -371,21 +371,23 @@ def run_ours(args, ws, rank, local):
     value = cells * args.steps * ws / (ms_max * 1e-3)
     clocks = clk.summary()
 
-    # ---- per-kernel times (eager, events on the bunch stream), same state and sequence
+    # ---- per-kernel times (eager, events on the bunch stream), the graph's sequence
+    # (guard fill + CFL dt in one pass, then the step), then the fill and the CFL pass alone
     dt_dev = torch.zeros(1, dtype=torch.float64, device=dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     for k in range(args.steps):
         ev[k][0].record(b.stream)
-        b.fill_guards()
+        b.fill_cfl_device(dt_dev)
         ev[k][1].record(b.stream)
-        b.cfl_dt_device(dt_dev)
-        ev[k][2].record(b.stream)
         b.step_device_dt(dt_dev)
+        ev[k][2].record(b.stream)
+        b.fill_guards()
         ev[k][3].record(b.stream)
+        b.cfl_dt_device(dt_dev)
+        ev[k][4].record(b.stream)
     b.stream.synchronize()
-    t_fill = np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])
-    t_cfl = np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)])
-    t_step = np.mean([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
+    mean = lambda i, j: float(np.mean([ev[k][i].elapsed_time(ev[k][j]) for k in range(args.steps)]))
+    t_fc, t_step, t_fill, t_cfl = mean(0, 1), mean(1, 2), mean(2, 3), mean(3, 4)
     code, msg = b.error()
     if code != 0:
         raise RuntimeError(f"device error during the benchmark: {msg}")
@@ -466,7 +468,7 @@ def run_ours(args, ws, rank, local):
                       "l2": f"inputs larger than L2 (state {b.nbytes / 1e9:.2f} GB per buffer)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "roofline": roof, "hbm_roofline": hbm_roof,
-           "kernels_ms": {"fill_guards": t_fill, "cfl_dt": t_cfl, "step": t_step},
+           "kernels_ms": {"fill_cfl": t_fc, "step": t_step, "fill_guards_alone": t_fill, "cfl_dt_alone": t_cfl},
            "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2,
                                "path": "guard fill + CFL dt + one step launch per patch, eager"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

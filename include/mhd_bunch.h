@@ -125,6 +125,13 @@ int mhd_bunch_fill_guards(mhd_bunch *b);
 int mhd_bunch_cfl_dt(mhd_bunch *b, double *dt_host);
 int mhd_bunch_cfl_dt_device(mhd_bunch *b, void *dt_dev);
 
+/* a1 + a2: the guard fill followed by the CFL dt into dt_dev (device double), as
+ * mhd_bunch_fill_guards then mhd_bunch_cfl_dt_device (the same ghost cells and, bitwise,
+ * the same dt); for equal patches on a regular grid in one pass over the state (one CTA per
+ * padded z-plane fills the plane's ghost cells, then takes the rates of its cells).  The
+ * captured graph and the advance calls use it.  Asynchronous, graph-capturable. */
+int mhd_bunch_fill_cfl_device(mhd_bunch *b, void *dt_dev);
+
 /* a3-a9: advance every patch by dt: reads U^n (ghosts filled) from the current buffer,
  * writes the interior cells and owned faces of U^{n+1} into the other one, then swaps
  * the two.  Ghost cells of the new state are stale until the next fill. */
@@ -167,7 +174,8 @@ int mhd_bunch_config_info(const mhd_bunch *b, int config, int *tile_x, int *tile
  * read from / written to that text file, keyed by device, precision and patch sizes. */
 int mhd_bunch_autotune(mhd_bunch *b, const char *cache_path, int *chosen);
 
-/* Capture nsteps of (fill guards -> CFL dt on the device -> step with the device dt) into
+/* Capture nsteps of (fill guards -> CFL dt on the device (mhd_bunch_fill_cfl_device) ->
+ * step with the device dt) into
  * a CUDA graph on the bound stream (which must not be the legacy default stream);
  * mhd_bunch_graph_launch replays it and swaps the buffers as the eager steps would.
  * dt_dev (device double[nsteps], may be NULL) receives the dt of each replayed step.

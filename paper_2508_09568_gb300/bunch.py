@@ -97,6 +97,10 @@ class MHDBunch:
         assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
         capi.check(self.lib.mhd_bunch_cfl_dt_device(self.h, ct.c_void_p(dt_dev.data_ptr())))
 
+    def fill_cfl_device(self, dt_dev: torch.Tensor):
+        """Guard fill then CFL dt into dt_dev (one pass on regular grids)."""
+        capi.check(self.lib.mhd_bunch_fill_cfl_device(self.h, ct.c_void_p(dt_dev.data_ptr())))
+
     def step(self, dt: float):
         capi.check(self.lib.mhd_bunch_step(self.h, float(dt)))
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "mhd_bunch_fill_guards": (I, [P]),
     "mhd_bunch_cfl_dt": (I, [P, DP]),
     "mhd_bunch_cfl_dt_device": (I, [P, P]),
+    "mhd_bunch_fill_cfl_device": (I, [P, P]),
     "mhd_bunch_step": (I, [P, D]),
     "mhd_bunch_step_device_dt": (I, [P, P]),
     "mhd_bunch_set_mode": (I, [P, I, I]),

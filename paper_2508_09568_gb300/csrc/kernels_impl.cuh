@@ -73,6 +73,16 @@ static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, con
 }
 
 template <typename R>
+static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, int npatch, const int64_t* nboff, int Zp,
+                                  double gamma, double courant, const double dxi[3], const int act[3], void* partial,
+                                  unsigned* counter, double* dt_out, unsigned* err, cudaStream_t s) {
+    fill_cfl_grid_kernel<R><<<(unsigned)npatch * (unsigned)Zp, 128, 0, s>>>(
+        static_cast<R*>(U), patches, nboff, Zp, gamma, courant, dxi[0], dxi[1], dxi[2], act[1], act[2],
+        static_cast<R*>(partial), counter, dt_out, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
 static cudaError_t launch_fill_interp(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list,
                                      int nlist, const int* slice, const double* t_old, const double* t_cur,
                                      const FillGeom& fg, unsigned* err, cudaStream_t s) {

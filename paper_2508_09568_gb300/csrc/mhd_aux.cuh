@@ -118,28 +118,32 @@ __global__ void __launch_bounds__(128) fill_grid_kernel(R* __restrict__ U, const
             x = c < gx ? c : pt.nx + c;
         }
     };
-    // two cells per thread and iteration: all 16 loads in flight before the stores
-    for (int k0 = threadIdx.x; k0 < ncnt; k0 += 2 * blockDim.x) {
-        const int k1 = k0 + blockDim.x;
-        const bool two = k1 < ncnt;
-        int x0, y0, x1 = 0, y1 = 0;
-        coord(k0, x0, y0);
-        if (two) coord(k1, x1, y1);
-        const R* s0 = U + neighbour_source(pt, nb, x0 - gx, y0 - gy, iz);
-        const R* s1 = two ? U + neighbour_source(pt, nb, x1 - gx, y1 - gy, iz) : s0;
-        R v0[8], v1[8];
+    // four cells per thread and pass: all their loads in flight before the stores
+    constexpr int NC = 4;
+    for (int k0 = threadIdx.x; k0 < ncnt; k0 += NC * blockDim.x) {
+        const R* src[NC];
+        R* dst[NC];
+        bool on[NC];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v0[q] = s0[q * vol];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v1[q] = s1[q * vol];
-        R* d0 = plane + (int64_t)y0 * X + x0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) d0[q * vol] = v0[q];
-        if (two) {
-            R* d1 = plane + (int64_t)y1 * X + x1;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) d1[q * vol] = v1[q];
+        for (int c = 0; c < NC; ++c) {
+            const int k = k0 + c * blockDim.x;
+            on[c] = k < ncnt;
+            int x = 0, y = 0;
+            if (on[c]) coord(k, x, y);
+            src[c] = U + neighbour_source(pt, nb, on[c] ? x - gx : 0, on[c] ? y - gy : 0, iz);
+            dst[c] = plane + (int64_t)y * X + x;
         }
+        R v[NC][8];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[c][q] = on[c] ? src[c][q * vol] : R(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (on[c]) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[c][q * vol] = v[c][q];
+            }
     }
 }
 
@@ -187,12 +191,13 @@ struct CflArgs {
 
 // CFL rate of the interior cell c (pointer to its rho) of a patch: sum over active axes of
 // (|u_d| + c_f,d) / dx_d, with the cell-centred field the mean of the cell's two faces
+// (the same with the cell's three high faces given)
 template <typename R>
-__device__ __forceinline__ R cell_rate(const R* c, int64_t vol, int sy, int sz, bool act1, bool act2, R gamma,
-                                       R gm1, R dxi0, R dxi1, R dxi2) {
-    const R bxc = R(0.5) * (c[5 * vol] + c[5 * vol + 1]);
-    const R byc = act1 ? R(0.5) * (c[6 * vol] + c[6 * vol + sy]) : c[6 * vol];
-    const R bzc = act2 ? R(0.5) * (c[7 * vol] + c[7 * vol + sz]) : c[7 * vol];
+__device__ __forceinline__ R cell_rate_faces(const R* c, int64_t vol, R bxh, R byh, R bzh, bool act1, bool act2,
+                                             R gamma, R gm1, R dxi0, R dxi1, R dxi2) {
+    const R bxc = R(0.5) * (c[5 * vol] + bxh);
+    const R byc = act1 ? R(0.5) * (c[6 * vol] + byh) : c[6 * vol];
+    const R bzc = act2 ? R(0.5) * (c[7 * vol] + bzh) : c[7 * vol];
     R q[8];
     cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
     const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
@@ -203,6 +208,13 @@ __device__ __forceinline__ R cell_rate(const R* c, int64_t vol, int sy, int sz, 
 }
 
 template <typename R>
+__device__ __forceinline__ R cell_rate(const R* c, int64_t vol, int sy, int sz, bool act1, bool act2, R gamma,
+                                       R gm1, R dxi0, R dxi1, R dxi2) {
+    return cell_rate_faces(c, vol, c[5 * vol + 1], act1 ? c[6 * vol + sy] : R(0), act2 ? c[7 * vol + sz] : R(0),
+                           act1, act2, gamma, gm1, dxi0, dxi1, dxi2);
+}
+
+template <typename R>
 __global__ void cfl_kernel(CflArgs<R> a) {
     __shared__ R red[32];
     __shared__ bool last;
@@ -210,17 +222,22 @@ __global__ void cfl_kernel(CflArgs<R> a) {
     const R dxi0 = R(a.dxi[0]), dxi1 = R(a.dxi[1]), dxi2 = R(a.dxi[2]);
     R vmax = R(0);
     bool bad = false;
+    // one warp per row of a patch (x along the lanes): the (z, y) of a row is computed once
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int p = blockIdx.x; p < a.npatch; p += gridDim.x) {
         const PatchDev pt = a.patches[p];
-        const int n = pt.nx * pt.ny * pt.nz;
+        const int rows = pt.ny * pt.nz;
         const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
         const int sy = pt.X, sz = pt.X * pt.Y;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
-            const R* c = a.U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
-            const R rate = cell_rate(c, vol, sy, sz, a.act[1] != 0, a.act[2] != 0, gamma, gm1, dxi0, dxi1, dxi2);
-            if (!isfinite((double)rate)) bad = true;
-            else vmax = rate > vmax ? rate : vmax;
+        for (int r = wid; r < rows; r += nw) {
+            const int z = r / pt.ny + pt.gz, y = r - (r / pt.ny) * pt.ny + pt.gy;
+            const R* row = a.U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + pt.gx;
+            for (int x = lane; x < pt.nx; x += 32) {
+                const R rate = cell_rate(row + x, vol, sy, sz, a.act[1] != 0, a.act[2] != 0, gamma, gm1, dxi0,
+                                         dxi1, dxi2);
+                if (!isfinite((double)rate)) bad = true;
+                else vmax = rate > vmax ? rate : vmax;
+            }
         }
     }
     if (bad) atomicOr(a.err, ERR_PHYS);
@@ -243,6 +260,119 @@ __global__ void cfl_kernel(CflArgs<R> a) {
         if (threadIdx.x == 0) {
             *a.dt_out = a.courant / (double)v;
             *a.counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// a1 + a2 fused for bunches of equal patches on a regular grid (the values of
+// fill_grid_kernel and the dt of cfl_kernel, bitwise): one CTA per padded z-plane of a
+// patch fills the plane's ghost cells, then (interior planes) takes the CFL rates of the
+// plane's cells.  Their high x- and y-faces are ghost cells the CTA has just written; the
+// high z-face of the top interior plane is read where the fill takes it from.  Each CTA
+// writes its maximum to partial[blockIdx.x]; the last CTA writes dt = courant / max.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
+                                                           const int64_t* __restrict__ nboff, int Zp, double gamma_d,
+                                                           double courant, double dxi0_d, double dxi1_d,
+                                                           double dxi2_d, int act1, int act2, R* partial,
+                                                           unsigned* counter, double* dt_out, unsigned* err) {
+    __shared__ R red[32];
+    __shared__ bool last;
+    const int p = blockIdx.x / Zp, z = blockIdx.x - p * Zp;
+    const PatchDev pt = patches[p];
+    const int64_t* nb = nboff + (int64_t)p * 27;
+    const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy;
+    const int64_t vol = (int64_t)X * Y * pt.Z;
+    const int iz = z - pt.gz;
+    const bool zghost = iz < 0 || iz >= pt.nz;
+    R* plane = U + pt.off + (int64_t)z * X * Y;
+    {   // ghost cells of the plane, as fill_grid_kernel
+        const int nfull = zghost ? X * Y : 2 * gy * X;
+        const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
+        auto coord = [&](int k, int& x, int& y) {
+            if (k < nfull) {
+                const int r = k / X;
+                x = k - r * X;
+                y = zghost ? r : (r < gy ? r : pt.ny + r);
+            } else {
+                const int k2 = k - nfull;
+                const int r = k2 / (2 * gx), c = k2 - r * (2 * gx);
+                y = gy + r;
+                x = c < gx ? c : pt.nx + c;
+            }
+        };
+        constexpr int NC = 4;
+        for (int k0 = threadIdx.x; k0 < ncnt; k0 += NC * blockDim.x) {
+            const R* src[NC];
+            R* dst[NC];
+            bool on[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int k = k0 + c * blockDim.x;
+                on[c] = k < ncnt;
+                int x = 0, y = 0;
+                if (on[c]) coord(k, x, y);
+                src[c] = U + neighbour_source(pt, nb, on[c] ? x - gx : 0, on[c] ? y - gy : 0, iz);
+                dst[c] = plane + (int64_t)y * X + x;
+            }
+            R v[NC][8];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[c][q] = on[c] ? src[c][q * vol] : R(0);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (on[c]) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dst[c][q * vol] = v[c][q];
+                }
+        }
+    }
+    __syncthreads();   // the plane's ghost faces are in place
+    R vmax = R(0);
+    bool bad = false;
+    if (!zghost) {
+        const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
+        const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
+        const bool top = iz + 1 == pt.nz;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int yy = wid; yy < pt.ny; yy += nw) {
+            const R* row = plane + (int64_t)(yy + gy) * X + gx;
+            for (int x = lane; x < pt.nx; x += 32) {
+                const R* c = row + x;
+                const R bxh = c[5 * vol + 1];
+                const R byh = act1 ? c[6 * vol + X] : R(0);
+                R bzh = R(0);
+                if (act2) bzh = top ? U[7 * vol + neighbour_source(pt, nb, x, yy, pt.nz)] : c[7 * vol + (int64_t)X * Y];
+                const R rate = cell_rate_faces(c, vol, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1,
+                                               dxi2);
+                if (!isfinite((double)rate)) bad = true;
+                else vmax = rate > vmax ? rate : vmax;
+            }
+        }
+    }
+    if (bad) atomicOr(err, ERR_PHYS);
+    const R bm = block_max(vmax, red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = bm;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        R v = R(0);
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+            const R w = ((volatile R*)partial)[k];
+            v = w > v ? w : v;
+        }
+        __syncthreads();
+        v = block_max(v, red);
+        if (threadIdx.x == 0) {
+            *dt_out = courant / (double)v;
+            *counter = 0u;
         }
     }
 }

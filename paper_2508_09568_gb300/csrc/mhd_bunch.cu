@@ -67,6 +67,7 @@ struct mhd_bunch {
     // neighbour offsets [npatch][27] of the table-driven guard fill (equal patches on a
     // regular grid only; null otherwise)
     int64_t* d_nboff = nullptr;
+    void* d_partial_fc = nullptr;        // per-plane partial maxima of the fused fill + CFL
     // tiles of each step configuration: natural (per patch) order and cost-sorted order
     struct Tiles {
         int4* d_nat = nullptr;
@@ -352,6 +353,24 @@ int do_cfl(mhd_bunch* b, double* dt_dev) {
     return MHD_OK;
 }
 
+// guard fill then CFL dt: one fused pass on regular grids, else the two kernels
+int do_fill_cfl(mhd_bunch* b, double* dt_dev) {
+    if (!b->d_nboff) {
+        int rc = do_fill(b);
+        return rc ? rc : do_cfl(b, dt_dev);
+    }
+    double dxi[3];
+    int act[3];
+    for (int d = 0; d < 3; ++d) {
+        dxi[d] = 1.0 / b->dx[d];
+        act[d] = active(b, d);
+    }
+    CK(b->K->fill_cfl(b->buf[b->cur], b->d_patches, b->npatch, b->d_nboff, b->hp[0].Z, b->gamma, b->courant, dxi, act,
+                      b->d_partial_fc, b->d_counter, dt_dev, b->d_err, b->stream));
+    b->launches++;
+    return MHD_OK;
+}
+
 int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
     if (b->cfg_index.empty()) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
     const int k = b->config < 0 ? default_config(b) : b->config;
@@ -606,7 +625,10 @@ int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patc
         const std::vector<int64_t> t = neighbour_table(b, patch_origin, domain_cells, owner, bs, M);
         cudaFree(b->d_nboff);
         b->d_nboff = nullptr;
+        cudaFree(b->d_partial_fc);
+        b->d_partial_fc = nullptr;
         if (!t.empty()) {
+            CK(cudaMalloc(&b->d_partial_fc, (size_t)b->npatch * b->hp[0].Z * b->rb));
             CK(cudaMalloc(&b->d_nboff, sizeof(int64_t) * t.size()));
             CK(cudaMemcpy(b->d_nboff, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice));
         }
@@ -675,6 +697,13 @@ int mhd_bunch_cfl_dt_device(mhd_bunch* b, void* dt_dev) {
     if (rc) return rc;
     if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
     return do_cfl(b, static_cast<double*>(dt_dev));
+}
+
+int mhd_bunch_fill_cfl_device(mhd_bunch* b, void* dt_dev) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
+    return do_fill_cfl(b, static_cast<double*>(dt_dev));
 }
 
 int mhd_bunch_cfl_dt(mhd_bunch* b, double* dt_host) {
@@ -845,8 +874,7 @@ int mhd_bunch_graph_capture(mhd_bunch* b, int nsteps, void* dt_dev) {
         CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         for (int s = 0; s < nsteps && rc == MHD_OK; ++s) {
             double* dt = dt_dev ? static_cast<double*>(dt_dev) + s : b->d_dt;
-            rc = do_fill(b);
-            if (!rc) rc = do_cfl(b, dt);
+            rc = do_fill_cfl(b, dt);
             if (!rc) rc = do_step(b, dt, 0.0);
         }
         cudaGraph_t g = nullptr;
@@ -900,8 +928,7 @@ int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t
     }
     CK(cudaMemcpyAsync(b->buf[b->cur], host_state, b->state_bytes, cudaMemcpyHostToDevice, b->stream));
     for (int s = 0; s < nsteps; ++s) {
-        rc = do_fill(b);
-        if (!rc) rc = do_cfl(b, b->d_dts + s);
+        rc = do_fill_cfl(b, b->d_dts + s);
         if (!rc) rc = do_step(b, b->d_dts + s, 0.0);
         if (rc) return rc;
     }
@@ -955,8 +982,7 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
         // guard fill and dt need the whole state; the update runs chunk by chunk and each
         // chunk goes back to the host as soon as it is done
         b->cur = A;
-        rc = do_fill(b);
-        if (!rc) rc = do_cfl(b, b->d_dts + s);
+        rc = do_fill_cfl(b, b->d_dts + s);
         for (int k = 0; k < K && !rc; ++k) {
             rc = do_step_range(b, b->d_dts + s, pb[k], pb[k + 1]);
             if (rc) break;
@@ -1148,6 +1174,7 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);
+    cudaFree(b->d_partial_fc);
     cudaFree(b->d_work);
     cudaFree(b->d_partial);
     cudaFree(b->d_counter);

@@ -58,6 +58,11 @@ struct PrecisionKernels {
     cudaError_t (*cfl_patch)(const void* U0, const void* U1, const PatchDev* patches, const int* list, int nlist,
                              const int* slice, double gamma, double courant, const double dxi[3], const int act[3],
                              double* dt_out, unsigned* err, cudaStream_t s);
+    // guard fill + CFL dt in one pass (regular grids: nboff the neighbour table, Zp the padded
+    // z extent); partial: npatch * Zp reals; counter: one zeroed unsigned
+    cudaError_t (*fill_cfl)(void* U, const PatchDev* patches, int npatch, const int64_t* nboff, int Zp, double gamma,
+                            double courant, const double dxi[3], const int act[3], void* partial, unsigned* counter,
+                            double* dt_out, unsigned* err, cudaStream_t s);
 };
 
 const PrecisionKernels& kernels_f32();

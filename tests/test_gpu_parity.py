@@ -118,6 +118,35 @@ def test_guard_fill_every_boundary_combination_bit_exact():
         b.close()
 
 
+def _outflow_box():
+    g0, U, meta = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=22)
+    bc = [[W.BC_OUTFLOW, W.BC_OUTFLOW], [W.BC_PERIODIC, W.BC_OUTFLOW], [W.BC_OUTFLOW, W.BC_PERIODIC]]
+    return W.uniform_geometry([24, 16, 16], [8, 8, 8], dx=g0.dx, bc=bc), U, meta
+
+
+@pytest.mark.parametrize("case", ["box", "outflow", "ot", "sod"])
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
+def test_fused_fill_cfl_equals_separate_passes(case, dtype):
+    """mhd_bunch_fill_cfl_device (one pass on regular grids) writes the ghost cells of the
+    guard fill and, bitwise, the dt of the separate CFL pass."""
+    geom, U, meta = {"box": lambda: W.small_box(ncell=(16, 24, 16), patch=(8, 8, 8), seed=25),
+                     "outflow": _outflow_box,
+                     "ot": lambda: W.orszag_tang(ncell=64, patch=16),
+                     "sod": lambda: W.sod(ncell=64, npatch=8)}[case]()
+    flat = rounded(W.to_patches(U, geom), dtype)
+    b = gpu_bunch(geom, flat, meta["gamma"], dtype)
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    b.fill_cfl_device(dt_dev)
+    b.stream.synchronize()
+    fused, dt_fused = b.download(), float(dt_dev.item())
+    b.upload(flat)
+    b.fill_guards()
+    dt_sep = b.cfl_dt()
+    assert np.array_equal(b.download(), fused)
+    assert dt_fused == dt_sep
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-14), (torch.float32, 2e-6)], ids=["f64", "f32"])
 def test_cfl_dt_matches_oracle(dtype, tol):
     for geom, U, meta in (W.small_box(seed=2), W.orszag_tang(ncell=64, patch=16), W.sod(64, 4)):
