@@ -147,9 +147,14 @@ static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsi
     a.riemann = h.riemann;
     const int bx = (h.max_cells + 255) / 256 < 64 ? (h.max_cells + 255) / 256 : 64;
     const dim3 grid(bx, h.npatch < 65535 ? h.npatch : 65535), blk(256);
-    dim3 fgrid(8, h.npatch < 65535 ? h.npatch : 65535);
+    const dim3 fgrid(bx, h.npatch < 65535 ? h.npatch : 65535);
+    const unsigned pgrid = (unsigned)h.npatch * (unsigned)h.Zp;   // planes (regular grids)
     int n = 0;
-    fill_kernel<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.U), h.patches, h.npatch, fg, err); ++n;
+    if (h.nboff)
+        fill_grid_kernel<R><<<pgrid, 128, 0, s>>>(static_cast<R*>(h.U), h.patches, h.nboff, h.Zp);
+    else
+        fill_kernel<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.U), h.patches, h.npatch, fg, err);
+    ++n;
     adj_fwd_prim<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_fwd_slopes<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_fwd_en<R><<<grid, blk, 0, s>>>(a); ++n;
@@ -163,7 +168,11 @@ static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsi
     adj_en<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_slopes<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_prim<R><<<grid, blk, 0, s>>>(a); ++n;
-    adj_fill_transpose<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.lam), h.patches, h.npatch, fg, err); ++n;
+    if (h.nboff)
+        adj_fill_transpose_grid<R><<<pgrid, 128, 0, s>>>(static_cast<R*>(h.lam), h.patches, h.nboff, h.Zp);
+    else
+        adj_fill_transpose<R><<<fgrid, 256, 0, s>>>(static_cast<R*>(h.lam), h.patches, h.npatch, fg, err);
+    ++n;
     if (nlaunch) *nlaunch = n;
     return cudaGetLastError();
 }

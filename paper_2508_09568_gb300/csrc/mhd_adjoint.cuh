@@ -563,4 +563,41 @@ __global__ void adj_fill_transpose(R* lam, const PatchDev* __restrict__ patches,
     }
 }
 
+// the same for equal patches on a regular grid: sources from the neighbour table (as
+// fill_grid_kernel), one CTA per padded z-plane of a patch walking the plane's ghost cells
+template <typename R>
+__global__ void adj_fill_transpose_grid(R* lam, const PatchDev* __restrict__ patches,
+                                        const int64_t* __restrict__ nboff, int Zp) {
+    const int p = blockIdx.x / Zp, z = blockIdx.x - p * Zp;
+    const PatchDev pt = patches[p];
+    const int64_t* nb = nboff + (int64_t)p * 27;
+    const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy;
+    const int64_t vol = (int64_t)X * Y * pt.Z;
+    const int iz = z - pt.gz;
+    const bool zghost = iz < 0 || iz >= pt.nz;
+    const int nfull = zghost ? X * Y : 2 * gy * X;
+    const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
+    R* plane = lam + pt.off + (int64_t)z * X * Y;
+    for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
+        int x, y;
+        if (k < nfull) {
+            const int r = k / X;
+            x = k - r * X;
+            y = zghost ? r : (r < gy ? r : pt.ny + r);
+        } else {
+            const int k2 = k - nfull;
+            const int r = k2 / (2 * gx), c = k2 - r * (2 * gx);
+            y = gy + r;
+            x = c < gx ? c : pt.nx + c;
+        }
+        R* s = lam + neighbour_source(pt, nb, x - gx, y - gy, iz);
+        R* d = plane + (int64_t)y * X + x;
+        for (int v = 0; v < 8; ++v) {
+            const R g = d[v * vol];
+            d[v * vol] = R(0);
+            if (g != R(0)) atomicAdd(&s[v * vol], g);
+        }
+    }
+}
+
 }  // namespace mhd

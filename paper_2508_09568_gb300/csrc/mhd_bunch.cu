@@ -1233,6 +1233,8 @@ extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, 
     for (int d = 0; d < 3; ++d) a.dxi[d] = 1.0 / b->dx[d];
     a.limiter = b->limiter;
     a.riemann = b->riemann;
+    a.nboff = b->d_nboff;
+    a.Zp = b->hp[0].Z;
     int n = 0;
     CK(b->K->adjoint(a, b->fg, b->d_err, b->stream, &n));
     b->launches += n;

@@ -32,6 +32,8 @@ struct AdjHostArgs {
     double dxi[3];
     int limiter;
     int riemann;
+    const int64_t* nboff;    // regular grids: neighbour table (table-driven fill and transpose), else null
+    int Zp;                  // padded z extent (regular grids)
 };
 
 // Kernel entry points of one precision (R = float or double).
