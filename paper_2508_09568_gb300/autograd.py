@@ -4,7 +4,9 @@ MHDStep.apply(U, bunch, dt) advances a state tensor (the flat state layout of th
 its GPU) by one step at fixed dt; its backward calls mhd_bunch_step_adjoint.  rollout()
 runs many steps keeping only every ckpt-th state; its backward recomputes each segment
 forward from its checkpoint and sweeps the adjoint back through it, so the memory held is
-about nsteps/ckpt + ckpt states.  Both the forward and the backward run in the library's
+about nsteps/ckpt + 2 ckpt states.  The recompute of segment k-1 runs on a twin handle
+(bunch.twin(): its own stream and work arrays) while the adjoint sweeps segment k on the
+bunch's stream; an event per segment orders the sweep after its recompute.  Both the forward and the backward run in the library's
 CUDA kernels; torch only holds the buffers.
 """
 from __future__ import annotations
@@ -94,19 +96,40 @@ class _Rollout(torch.autograd.Function):
         bunch, dt, n, k = ctx.bunch, ctx.dt, ctx.nsteps, ctx.ckpt
         cur_stream = torch.cuda.current_stream(g.device)
         bunch.stream.wait_stream(cur_stream)
-        with torch.cuda.stream(bunch.stream):
-            lam = g.contiguous().clone()
-            for seg in reversed(range(len(ctx.ckpts))):
-                s0 = seg * k
-                s1 = min(n, s0 + k)
-                # recompute the segment's inputs from its checkpoint
+        twin = bunch.twin()
+        # the checkpoints were written on the bunch's stream
+        twin.stream.wait_stream(bunch.stream)
+
+        def recompute(seg):
+            # the segment's inputs from its checkpoint, on the twin's stream (each step's
+            # guard fill rewrites the ghosts of its input, which the adjoint fills anew)
+            s0 = seg * k
+            s1 = min(n, s0 + k)
+            with torch.cuda.stream(twin.stream):
                 states = [ctx.ckpts[seg]]
                 for _ in range(s0, s1 - 1):
                     nxt = torch.empty_like(states[-1])
-                    _step_into(bunch, states[-1].clone(), nxt, dt)
+                    _step_into(twin, states[-1], nxt, dt)
                     states.append(nxt)
+                done = torch.cuda.Event()
+                done.record(twin.stream)
+            for t in states:
+                t.record_stream(bunch.stream)
+            return states, done
+
+        with torch.cuda.stream(bunch.stream):
+            lam = g.contiguous().clone()
+        nseg = len(ctx.ckpts)
+        pending = recompute(nseg - 1)
+        for seg in reversed(range(nseg)):
+            states, done = pending
+            if seg > 0:
+                pending = recompute(seg - 1)
+            bunch.stream.wait_event(done)
+            with torch.cuda.stream(bunch.stream):
                 for U in reversed(states):
                     lam = _adjoint(bunch, U, lam, dt)
+        with torch.cuda.stream(bunch.stream):
             _restore(bunch)
         cur_stream.wait_stream(bunch.stream)
         lam.record_stream(cur_stream)

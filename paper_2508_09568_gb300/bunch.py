@@ -28,6 +28,8 @@ class MHDBunch:
             raise RuntimeError("MHDBunch needs a CUDA device (no CPU fallback)")
         self.lib = capi.load()
         self.geom = geom
+        self._params = dict(gamma=gamma, courant=courant, limiter=limiter, riemann=riemann)
+        self._twin = None
         self.dtype = dtype
         self.device = torch.device(device)
         self.rb = 4 if dtype == torch.float32 else 8
@@ -191,7 +193,19 @@ class MHDBunch:
         capi.check(self.lib.mhd_bunch_launch_count(self.h, ct.byref(n)))
         return n.value
 
+    def twin(self) -> "MHDBunch":
+        """A second handle on the same geometry and parameters with its own stream, state
+        buffers and work arrays (created on first use, closed with this one), so that two
+        step sequences can run concurrently; every mode and tile configuration computes the
+        same state, so the twin's steps equal this handle's."""
+        if self._twin is None:
+            self._twin = MHDBunch(self.geom, self.dtype, device=str(self.device), **self._params)
+        return self._twin
+
     def close(self):
+        if getattr(self, "_twin", None) is not None:
+            self._twin.close()
+            self._twin = None
         if getattr(self, "h", None):
             self.stream.synchronize()
             self.lib.mhd_bunch_destroy(self.h)

@@ -1,6 +1,8 @@
 // Instantiation helpers shared by the per-precision translation units.
 #pragma once
 
+#include <algorithm>
+
 #include "mhd_adjoint.cuh"
 #include "mhd_aux.cuh"
 #include "mhd_launch.h"
@@ -145,7 +147,14 @@ static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsi
     for (int d = 0; d < 3; ++d) a.dxi[d] = h.dxi[d];
     a.limiter = h.limiter;
     a.riemann = h.riemann;
-    const int bx = (h.max_cells + 255) / 256 < 64 ? (h.max_cells + 255) / 256 : 64;
+    // x-blocks per patch: 64, or (FP64, whose kernels are longer) enough for ~8 blocks per
+    // SM on small bunches; never more than one thread per padded cell
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;
+    const int bcap = (h.max_cells + 255) / 256;
+    const int bwant = sizeof(R) == 8 ? std::max(64, (8 * sms + h.npatch - 1) / h.npatch) : 64;
+    const int bx = std::max(1, std::min(bcap, bwant));
     const dim3 grid(bx, h.npatch < 65535 ? h.npatch : 65535), blk(256);
     const dim3 fgrid(bx, h.npatch < 65535 ? h.npatch : 65535);
     const unsigned pgrid = (unsigned)h.npatch * (unsigned)h.Zp;   // planes (regular grids)
@@ -161,8 +170,8 @@ static cudaError_t launch_adjoint(const AdjHostArgs& h, const FillGeom& fg, unsi
     adj_fwd_bh<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_fwd_wh<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_init<R><<<grid, blk, 0, s>>>(a); ++n;
-    adj_faces<R><<<grid, blk, 0, s>>>(a); ++n;
-    adj_edges<R><<<grid, blk, 0, s>>>(a); ++n;
+    adj_faces<R><<<dim3(grid.x, grid.y, 3), blk, 0, s>>>(a); ++n;
+    adj_edges<R><<<dim3(grid.x, grid.y, 3), blk, 0, s>>>(a); ++n;
     adj_pred<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_bh<R><<<grid, blk, 0, s>>>(a); ++n;
     adj_en<R><<<grid, blk, 0, s>>>(a); ++n;

@@ -9,6 +9,10 @@
 // The last kernel is the transpose of the guard fill: the cotangent that reached a ghost
 // copy is added to the interior cell it copies.
 //
+// Occupancy: the face and edge kernels (the HLLD / 2D-HLL VJPs) are capped at 128
+// registers (two 256-thread blocks per SM) and take their direction from the grid's z
+// index, so each thread handles one face or edge; the cell kernels are capped at 85.
+//
 // Work arrays (fields of one value per padded cell; index coff[p] + (z*Y + y)*X + x):
 //   W(8) primitives, DW(24) slopes [d][k], FS(6) face-field slopes, EN(3) time-n edge
 //   EMFs, BH(3) predicted low-face fields, WH(8) predicted cell state; and the same 52
@@ -248,11 +252,11 @@ __global__ void adj_init(AdjArgs<R> a) {
 // faces: the HLLD flux through the low c-face of cells with normal index in [g, g+n] and
 // transverse indices in the interior
 template <typename R>
-__global__ void adj_faces(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 2) adj_faces(AdjArgs<R> a) {
     const R gamma = R(a.gamma), gm1i = R(1.0 / (a.gamma - 1.0)), eps = R(a.eps);
     ADJ_FOR_REGION(a, 0, 1, {
         const int64_t i = C.at(x, y, z);
-        for (int c = 0; c < 3; ++c) {
+        for (int c = blockIdx.z; c < 3; c += gridDim.z) {   // face direction: one per grid z-slice
             const int t1 = (c + 1) % 3, t2 = (c + 2) % 3;
             const int v3[3] = {x, y, z};
             const int lim[3] = {pt.gx + pt.nx, pt.gy + pt.ny, pt.gz + pt.nz};
@@ -340,10 +344,10 @@ __device__ __forceinline__ void adj_corner_scatter(const AdjArgs<R>& a, const Ce
 // edges: the 2D HLL EMF on the edge low in (a, b) of cells with a, b indices in [g, g+n]
 // and the e index in the interior
 template <typename R>
-__global__ void adj_edges(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 2) adj_edges(AdjArgs<R> a) {
     const R gamma = R(a.gamma);
     ADJ_FOR_REGION(a, 0, 1, {
-        for (int e = 0; e < 3; ++e) {
+        for (int e = blockIdx.z; e < 3; e += gridDim.z) {   // edge direction: one per grid z-slice
             const int A = (e + 1) % 3, B = (e + 2) % 3;
             const int v3[3] = {x, y, z};
             const int lim[3] = {pt.gx + pt.nx, pt.gy + pt.ny, pt.gz + pt.nz};
@@ -375,7 +379,7 @@ __global__ void adj_edges(AdjArgs<R> a) {
 
 // predictor: lWH -> lW, lDW (Hancock) and lBH (cell-centred predicted field = face mean)
 template <typename R>
-__global__ void adj_pred(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) adj_pred(AdjArgs<R> a) {
     const R hdt = R(0.5 * a.dt), gamma = R(a.gamma);
     ADJ_FOR_REGION(a, -1, 1, {
         const int64_t i = C.at(x, y, z);
@@ -408,7 +412,7 @@ __global__ void adj_pred(AdjArgs<R> a) {
 
 // predicted faces: bh_c = B_c + dt/2 (dx_A^-1 (EN_B(+A) - EN_B) - dx_B^-1 (EN_A(+B) - EN_A))
 template <typename R>
-__global__ void adj_bh(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) adj_bh(AdjArgs<R> a) {
     const R hdt = R(0.5 * a.dt);
     ADJ_FOR_REGION(a, -1, 2, {
         const int64_t i = C.at(x, y, z);
@@ -432,7 +436,7 @@ __global__ void adj_bh(AdjArgs<R> a) {
 
 // time-n edge EMF: E = <v_a><B_b> - <v_b><B_a>
 template <typename R>
-__global__ void adj_en(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) adj_en(AdjArgs<R> a) {
     ADJ_FOR_REGION(a, -1, 2, {
         const int64_t i = C.at(x, y, z);
         for (int e = 0; e < 3; ++e) {
@@ -460,7 +464,7 @@ __global__ void adj_en(AdjArgs<R> a) {
 
 // limited slopes of the primitives and of the face fields
 template <typename R>
-__global__ void adj_slopes(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) adj_slopes(AdjArgs<R> a) {
     ADJ_FOR_REGION(a, -1, 2, {
         const int64_t i = C.at(x, y, z);
         const bool inner = x <= pt.gx + pt.nx && y <= pt.gy + pt.ny && z <= pt.gz + pt.nz;
@@ -501,7 +505,7 @@ __global__ void adj_slopes(AdjArgs<R> a) {
 
 // primitives: lW -> lU (rho, momenta, E) and the two faces of each field component
 template <typename R>
-__global__ void adj_prim(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) adj_prim(AdjArgs<R> a) {
     const R gm1 = R(a.gamma - 1.0);
     ADJ_FOR_REGION(a, -2, 2, {
         const int64_t i = C.at(x, y, z);
