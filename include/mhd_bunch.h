@@ -151,8 +151,13 @@ int mhd_bunch_step_device_dt(mhd_bunch *b, const void *dt_dev);
  * div B hold inside patches; faces shared by patches at different times are updated by
  * each side with its own fluxes.  Returns the rounds and the patch updates done; after
  * the call the current buffer holds every patch at the common time + t_span (ghost cells
- * not meaningful).  max_rounds >= 1; MHD_ESTATE if max_rounds ran out first.  Synchronises
- * the bound stream every round (the host schedules). */
+ * not meaningful).  max_rounds >= 1; MHD_ESTATE if max_rounds ran out first (*rounds and
+ * the record still cover the rounds done); MHD_EPHYS if a patch's dt came out
+ * non-positive or non-finite (later rounds are skipped; the state is then not meaningful).
+ * The schedule runs on the device: each round is five stream-ordered launches (schedule,
+ * guard fill at the patches' own times, per-patch CFL dt, dt clipping, update); the host
+ * enqueues 32 rounds at a time and synchronises the bound stream once per 32 rounds to
+ * read their record. */
 int mhd_bunch_advance_async(mhd_bunch *b, double t_span, int max_rounds, int *rounds,
                             int64_t *patch_updates);
 /* The record of round `round` of the last mhd_bunch_advance_async: its patches (in

@@ -20,6 +20,7 @@ static StepArgs<R> to_args(const StepHostArgs& h) {
     a.patches = h.patches;
     a.tiles = h.tiles;
     a.ntiles = h.ntiles;
+    a.ntiles_dev = h.ntiles_dev;
     a.dynamic = h.dynamic;
     a.work = h.work;
     a.dt_ptr = h.dt_ptr;
@@ -86,24 +87,28 @@ static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, int npatch,
 
 template <typename R>
 static cudaError_t launch_fill_interp(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list,
-                                     int nlist, const int* slice, const double* t_old, const double* t_cur,
-                                     const FillGeom& fg, unsigned* err, cudaStream_t s) {
+                                     int nlist, const int* nlist_dev, int grid_y, const int* slice,
+                                     const double* t_old, const double* t_cur, const FillGeom& fg, unsigned* err,
+                                     cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    dim3 grid(8, nlist < 65535 ? nlist : 65535);
+    const int gy = std::min(std::min(nlist, grid_y > 0 ? grid_y : nlist), 65535);
+    dim3 grid(32, gy);
     fill_interp_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U0), static_cast<R*>(U1), patches, npatch, list, nlist,
-                                               slice, t_old, t_cur, fg, err);
+                                               nlist_dev, slice, t_old, t_cur, fg, err);
     return cudaGetLastError();
 }
 
 template <typename R>
 static cudaError_t launch_cfl_patch(const void* U0, const void* U1, const PatchDev* patches, const int* list,
-                                   int nlist, const int* slice, double gamma, double courant, const double dxi[3],
-                                   const int act[3], double* dt_out, unsigned* err, cudaStream_t s) {
+                                   int nlist, const int* nlist_dev, int grid_y, const int* slice, double gamma,
+                                   const double dxi[3], const int act[3], unsigned long long* rate_max,
+                                   unsigned* err, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    const int grid = nlist < 65535 ? nlist : 65535;
+    const int gy = std::min(std::min(nlist, grid_y > 0 ? grid_y : nlist), 65535);
+    dim3 grid(16, gy);
     cfl_patch_kernel<R><<<grid, 256, 0, s>>>(static_cast<const R*>(U0), static_cast<const R*>(U1), patches, list,
-                                             nlist, slice, gamma, courant, dxi[0], dxi[1], dxi[2], act[1], act[2],
-                                             dt_out, err);
+                                             nlist, nlist_dev, slice, gamma, dxi[0], dxi[1], dxi[2], act[1], act[2],
+                                             rate_max, err);
     return cudaGetLastError();
 }
 

@@ -388,10 +388,11 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
 // (or equal slice times) takes the current slice exactly, w <= 0 the previous one.
 template <typename R>
 __global__ void fill_interp_kernel(R* __restrict__ U0, R* __restrict__ U1, const PatchDev* __restrict__ patches,
-                                   int npatch, const int* __restrict__ list, int nlist, const int* __restrict__ slice,
-                                   const double* __restrict__ t_old, const double* __restrict__ t_cur, FillGeom fg,
-                                   unsigned* err) {
-    for (int L = blockIdx.y; L < nlist; L += gridDim.y) {
+                                   int npatch, const int* __restrict__ list, int nlist, const int* nlist_dev,
+                                   const int* __restrict__ slice, const double* __restrict__ t_old,
+                                   const double* __restrict__ t_cur, FillGeom fg, unsigned* err) {
+    const int nl = nlist_dev ? min(*nlist_dev, nlist) : nlist;
+    for (int L = blockIdx.y; L < nl; L += gridDim.y) {
         const int p = list[L];
         const PatchDev pt = patches[p];
         const int ng = ghost_count(pt);
@@ -436,17 +437,23 @@ __global__ void fill_interp_kernel(R* __restrict__ U0, R* __restrict__ U1, const
     }
 }
 
-// a2 per listed patch: dt_out[p] = courant / (max CFL rate over the patch's interior cells)
-// of its current slice (one block per listed patch).  Non-finite rates set ERR_PHYS.
+// a2 per listed patch: the maximum CFL rate over the patch's interior cells of its current
+// slice, as the bit pattern of a non-negative double in rate_max[p] (zeroed beforehand;
+// blocks along x share a patch and combine with an integer atomic max, which orders
+// non-negative doubles as their values, so the result is exact and order independent).
+// The dt, courant / max rate, is taken by the asynchronous scheduler.  Non-finite rates
+// set ERR_PHYS and are left out of the maximum.
 template <typename R>
 __global__ void cfl_patch_kernel(const R* __restrict__ U0, const R* __restrict__ U1,
                                  const PatchDev* __restrict__ patches, const int* __restrict__ list, int nlist,
-                                 const int* __restrict__ slice, double gamma_d, double courant, double dxi0_d,
-                                 double dxi1_d, double dxi2_d, int act1, int act2, double* dt_out, unsigned* err) {
+                                 const int* nlist_dev, const int* __restrict__ slice, double gamma_d, double dxi0_d,
+                                 double dxi1_d, double dxi2_d, int act1, int act2, unsigned long long* rate_max,
+                                 unsigned* err) {
     __shared__ R red[32];
+    const int nl = nlist_dev ? min(*nlist_dev, nlist) : nlist;
     const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
     const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
-    for (int L = blockIdx.x; L < nlist; L += gridDim.x) {
+    for (int L = blockIdx.y; L < nl; L += gridDim.y) {
         const int p = list[L];
         const PatchDev pt = patches[p];
         const int n = pt.nx * pt.ny * pt.nz;
@@ -454,7 +461,7 @@ __global__ void cfl_patch_kernel(const R* __restrict__ U0, const R* __restrict__
         const R* base = (slice[p] ? U1 : U0) + pt.off;
         R vmax = R(0);
         bool bad = false;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
             const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
             const R* c = base + ((int64_t)z * pt.Y + y) * pt.X + x;
             const R rate = cell_rate(c, vol, pt.X, pt.X * pt.Y, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
@@ -463,7 +470,8 @@ __global__ void cfl_patch_kernel(const R* __restrict__ U0, const R* __restrict__
         }
         if (bad) atomicOr(err, ERR_PHYS);
         const R bm = block_max(vmax, red);
-        if (threadIdx.x == 0) dt_out[p] = courant / (double)bm;
+        if (threadIdx.x == 0 && bm > R(0))
+            atomicMax(&rate_max[p], (unsigned long long)__double_as_longlong((double)bm));
         __syncthreads();
     }
 }

@@ -19,6 +19,7 @@
 
 #include "../../include/mhd_bunch.h"
 #include "mhd_launch.h"
+#include "mhd_sched.cuh"
 
 using namespace mhd;
 
@@ -101,9 +102,23 @@ struct mhd_bunch {
     double* d_told = nullptr;
     double* d_tcur = nullptr;
     double* d_dtp = nullptr;
-    int* d_list = nullptr;
     int4* d_atiles = nullptr;
     int atiles_cap = 0;
+    // device scheduler: neighbour lists (CSR), tile index of the chosen configuration, the
+    // record of a batch of rounds (list, dt, arrival flag, count per round), tile count,
+    // abort flag
+    int* d_nb_off = nullptr;
+    int* d_nb_idx = nullptr;
+    int* d_tfirst = nullptr;
+    int* d_tcount = nullptr;
+    int* d_rows_list = nullptr;
+    double* d_rows_dt = nullptr;
+    unsigned char* d_rows_last = nullptr;
+    int* d_rows_n = nullptr;
+    int* d_ntiles = nullptr;
+    unsigned* d_abort = nullptr;
+    int* d_ready = nullptr;                 // readiness flag per patch
+    unsigned long long* d_rmax = nullptr;   // maximum CFL rate per patch (double bits)
     std::vector<std::vector<int>> log_patches;
     std::vector<std::vector<double>> log_dts;
     // host-streamed advance: library-owned copy streams and per-chunk events
@@ -277,6 +292,7 @@ StepHostArgs step_args(mhd_bunch* b, const double* dt_ptr, double dt_val) {
     a.patches = b->d_patches;
     a.tiles = nullptr;
     a.ntiles = 0;
+    a.ntiles_dev = nullptr;
     a.dynamic = 0;
     a.work = b->d_work;
     a.dt_ptr = dt_ptr;
@@ -483,15 +499,35 @@ void build_neighbours(mhd_bunch* b) {
     }
 }
 
+constexpr int kAsyncRows = 32;   // rounds enqueued between two reads of the record
+
 int ensure_async(mhd_bunch* b) {
     if (b->nbrs.empty()) build_neighbours(b);
     const size_t P = (size_t)b->npatch;
     if (!b->d_slice) {
+        std::vector<int> off(P + 1, 0), idx;
+        for (size_t p = 0; p < P; ++p) {
+            idx.insert(idx.end(), b->nbrs[p].begin(), b->nbrs[p].end());
+            off[p + 1] = (int)idx.size();
+        }
         CK(cudaMalloc(&b->d_slice, sizeof(int) * P));
         CK(cudaMalloc(&b->d_told, sizeof(double) * P));
         CK(cudaMalloc(&b->d_tcur, sizeof(double) * P));
         CK(cudaMalloc(&b->d_dtp, sizeof(double) * P));
-        CK(cudaMalloc(&b->d_list, sizeof(int) * P));
+        CK(cudaMalloc(&b->d_nb_off, sizeof(int) * (P + 1)));
+        CK(cudaMalloc(&b->d_nb_idx, sizeof(int) * std::max<size_t>(idx.size(), 1)));
+        CK(cudaMalloc(&b->d_tfirst, sizeof(int) * P));
+        CK(cudaMalloc(&b->d_tcount, sizeof(int) * P));
+        CK(cudaMalloc(&b->d_rows_list, sizeof(int) * P * kAsyncRows));
+        CK(cudaMalloc(&b->d_rows_dt, sizeof(double) * P * kAsyncRows));
+        CK(cudaMalloc(&b->d_rows_last, P * kAsyncRows));
+        CK(cudaMalloc(&b->d_rows_n, sizeof(int) * kAsyncRows));
+        CK(cudaMalloc(&b->d_ntiles, sizeof(int)));
+        CK(cudaMalloc(&b->d_abort, sizeof(unsigned)));
+        CK(cudaMalloc(&b->d_ready, sizeof(int) * P));
+        CK(cudaMalloc(&b->d_rmax, sizeof(unsigned long long) * P));
+        CK(cudaMemcpy(b->d_nb_off, off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+        if (!idx.empty()) CK(cudaMemcpy(b->d_nb_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
     }
     return MHD_OK;
 }
@@ -1019,8 +1055,6 @@ int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* ro
     if (rc) return rc;
     const int P = b->npatch;
     const int A = b->cur;
-    std::vector<double> t_old(P, 0.0), t_cur(P, 0.0), dtp(P, 0.0);
-    std::vector<int> slice(P, 0);
     double dxi[3];
     int act[3];
     for (int d = 0; d < 3; ++d) {
@@ -1033,93 +1067,105 @@ int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* ro
     int occ = 1;
     CK(L.occupancy(&occ));
     occ = std::max(occ, 1);
+    if (T.n > b->atiles_cap) {
+        cudaFree(b->d_atiles);
+        b->d_atiles = nullptr;
+        CK(cudaMalloc(&b->d_atiles, sizeof(int4) * T.n));
+        b->atiles_cap = T.n;
+    }
+    cudaStream_t st = b->stream;
+    // every patch at the common time 0 in the current buffer (slice 0)
+    CK(cudaMemcpyAsync(b->d_tfirst, T.first.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_tcount, T.count.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(b->d_slice, 0, sizeof(int) * P, st));
+    CK(cudaMemsetAsync(b->d_told, 0, sizeof(double) * P, st));
+    CK(cudaMemsetAsync(b->d_tcur, 0, sizeof(double) * P, st));
+    CK(cudaMemsetAsync(b->d_abort, 0, sizeof(unsigned), st));
     b->log_patches.clear();
     b->log_dts.clear();
+
+    // the previous round's commit (prev < 0: none)
+    auto commit = [&](int prev) -> cudaError_t {
+        if (prev < 0) return cudaSuccess;
+        async_commit_kernel<<<std::max(1, b->nsm), 256, 0, st>>>(
+            b->d_rows_list + (size_t)prev * P, b->d_rows_n + prev, b->d_rows_dt + (size_t)prev * P,
+            b->d_rows_last + (size_t)prev * P, t_span, b->d_told, b->d_tcur, b->d_slice);
+        ++b->launches;
+        return cudaGetLastError();
+    };
+    StepHostArgs a = step_args(b, nullptr, 0.0);
+    a.U = b->buf[A];
+    a.Unew = b->buf[1 - A];
+    a.slice = b->d_slice;
+    a.dt_patch = b->d_dtp;
+    a.tiles = b->d_atiles;
+    a.ntiles = T.n;
+    a.ntiles_dev = b->d_ntiles;
+    a.dynamic = 1;
+    const int step_grid = std::min(T.n, b->nsm * occ);
+    const int list_blocks = std::max(1, 2 * b->nsm);
+
     int64_t updates = 0;
-    int r = 0;
-    for (; r < max_rounds; ++r) {
-        // ready: not yet at t_span and not ahead of any neighbour
-        std::vector<int> list;
-        for (int p = 0; p < P; ++p) {
-            if (!(t_cur[p] < t_span)) continue;
-            bool ok = true;
-            for (int q : b->nbrs[p])
-                if (t_cur[q] < t_cur[p]) { ok = false; break; }
-            if (ok) list.push_back(p);
+    int r = 0, prev = -1;
+    std::vector<int> hn(kAsyncRows), hl;
+    std::vector<double> hd;
+    bool done = false;
+    while (!done && r < max_rounds) {
+        const int kb = std::min(kAsyncRows, max_rounds - r);
+        for (int i = 0; i < kb; ++i) {
+            int* row = b->d_rows_list + (size_t)i * P;
+            int* nrow = b->d_rows_n + i;
+            CK(commit(prev));
+            async_ready_kernel<<<(P + 255) / 256, 256, 0, st>>>(P, b->d_nb_off, b->d_nb_idx, b->d_tcur, t_span,
+                                                                 b->d_abort, b->d_ready);
+            async_list_kernel<<<1, kSchedThreads, 0, st>>>(P, b->d_ready, b->d_tfirst, b->d_tcount, T.d_nat, row,
+                                                           nrow, b->d_atiles, b->d_ntiles, b->d_rmax);
+            CK(cudaGetLastError());
+            // guard zones at each patch's own time, then its own CFL dt, clipped
+            CK(b->K->fill_interp(b->buf[A], b->buf[1 - A], b->d_patches, P, row, P, nrow, list_blocks, b->d_slice,
+                                 b->d_told, b->d_tcur, b->fg, b->d_err, st));
+            CK(b->K->cfl_patch(b->buf[A], b->buf[1 - A], b->d_patches, row, P, nrow, list_blocks, b->d_slice,
+                               b->gamma, dxi, act, b->d_rmax, b->d_err, st));
+            async_clamp_kernel<<<std::max(1, (P + 255) / 256), 256, 0, st>>>(
+                row, nrow, b->d_rmax, b->courant, b->d_tcur, t_span, b->d_dtp, b->d_rows_dt + (size_t)i * P,
+                b->d_rows_last + (size_t)i * P, b->d_abort, b->d_err);
+            CK(cudaGetLastError());
+            // the update of the listed tiles, current slice -> the other, each by its own dt
+            CK(L.launch(&a, step_grid, st));
+            b->launches += 6;
+            prev = i;
         }
-        if (list.empty()) break;
-        const int n = (int)list.size();
-        CK(cudaMemcpyAsync(b->d_list, list.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream));
-        CK(cudaMemcpyAsync(b->d_slice, slice.data(), sizeof(int) * P, cudaMemcpyHostToDevice, b->stream));
-        CK(cudaMemcpyAsync(b->d_told, t_old.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
-        CK(cudaMemcpyAsync(b->d_tcur, t_cur.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
-        // guard zones at each patch's own time, then its own CFL dt
-        CK(b->K->fill_interp(b->buf[A], b->buf[1 - A], b->d_patches, P, b->d_list, n, b->d_slice, b->d_told,
-                             b->d_tcur, b->fg, b->d_err, b->stream));
-        CK(b->K->cfl_patch(b->buf[A], b->buf[1 - A], b->d_patches, b->d_list, n, b->d_slice, b->gamma, b->courant,
-                           dxi, act, b->d_dtp, b->d_err, b->stream));
-        b->launches += 2;
-        CK(cudaMemcpyAsync(dtp.data(), b->d_dtp, sizeof(double) * P, cudaMemcpyDeviceToHost, b->stream));
-        CK(cudaStreamSynchronize(b->stream));
-        std::vector<double> used(n);
-        std::vector<bool> last(n, false);
-        for (int i = 0; i < n; ++i) {
-            const int p = list[i];
-            const double rem = t_span - t_cur[p];
-            if (!(dtp[p] > 0) || !std::isfinite(dtp[p])) {
-                int code = 0;
-                read_error(b, &code, nullptr, 0);
-                return code ? code : fail(MHD_EPHYS, "non-finite local time step");
+        // the batch's record; an empty round means every patch has arrived (the patch at
+        // the earliest time is always ready) or a round failed
+        CK(cudaMemcpyAsync(hn.data(), b->d_rows_n, sizeof(int) * kb, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int m = 0;
+        while (m < kb && hn[m] > 0) ++m;
+        if (m > 0) {
+            hl.resize((size_t)m * P);
+            hd.resize((size_t)m * P);
+            CK(cudaMemcpyAsync(hl.data(), b->d_rows_list, sizeof(int) * m * P, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hd.data(), b->d_rows_dt, sizeof(double) * m * P, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int i = 0; i < m; ++i) {
+                b->log_patches.emplace_back(hl.begin() + (size_t)i * P, hl.begin() + (size_t)i * P + hn[i]);
+                b->log_dts.emplace_back(hd.begin() + (size_t)i * P, hd.begin() + (size_t)i * P + hn[i]);
+                updates += hn[i];
             }
-            if (dtp[p] >= rem) {
-                dtp[p] = rem;
-                last[i] = true;
-            }
-            used[i] = dtp[p];
         }
-        CK(cudaMemcpyAsync(b->d_dtp, dtp.data(), sizeof(double) * P, cudaMemcpyHostToDevice, b->stream));
-        // the update of the listed patches, each by its own dt, current slice -> the other
-        std::vector<int4> tl;   // the listed patches' tiles (contiguous per patch in the natural order)
-        for (int p : list)
-            tl.insert(tl.end(), T.nat_h.begin() + T.first[p], T.nat_h.begin() + T.first[p] + T.count[p]);
-        if ((int)tl.size() > b->atiles_cap) {
-            cudaFree(b->d_atiles);
-            b->d_atiles = nullptr;
-            CK(cudaMalloc(&b->d_atiles, sizeof(int4) * T.n));
-            b->atiles_cap = T.n;
-        }
-        CK(cudaMemcpyAsync(b->d_atiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, b->stream));
-        StepHostArgs a = step_args(b, nullptr, 0.0);
-        a.U = b->buf[A];
-        a.Unew = b->buf[1 - A];
-        a.slice = b->d_slice;
-        a.dt_patch = b->d_dtp;
-        a.tiles = b->d_atiles;
-        a.ntiles = (int)tl.size();
-        a.dynamic = 1;
-        CK(L.launch(&a, std::min((int)tl.size(), b->nsm * occ), b->stream));
-        b->launches++;
-        for (int i = 0; i < n; ++i) {
-            const int p = list[i];
-            t_old[p] = t_cur[p];
-            t_cur[p] = last[i] ? t_span : t_cur[p] + used[i];
-            slice[p] ^= 1;
-        }
-        updates += n;
-        b->log_patches.push_back(list);
-        b->log_dts.push_back(used);
+        r += m;
+        if (m < kb) done = true;
     }
-    // gather: every patch's final slice into the current buffer (runs of consecutive patches)
-    for (int p = 0; p < P;) {
-        if (!slice[p]) { ++p; continue; }
-        int q = p;
-        while (q + 1 < P && slice[q + 1]) ++q;
-        const size_t lo = (size_t)b->offs[p] * b->rb;
-        const size_t hi = q + 1 < P ? (size_t)b->offs[q + 1] * b->rb : b->state_bytes;
-        CK(cudaMemcpyAsync(static_cast<char*>(b->buf[A]) + lo, static_cast<char*>(b->buf[1 - A]) + lo, hi - lo,
-                           cudaMemcpyDeviceToDevice, b->stream));
-        p = q + 1;
-    }
+    // commit the last round, then gather every patch's final slice into the current buffer
+    CK(commit(prev));
+    async_gather_kernel<<<dim3(16, std::min(P, 65535)), 256, 0, st>>>(
+        static_cast<unsigned*>(b->buf[A]), static_cast<const unsigned*>(b->buf[1 - A]), b->d_patches, P,
+        b->d_slice, b->rb / 4);
+    CK(cudaGetLastError());
+    ++b->launches;
+    std::vector<double> t_cur(P);
+    CK(cudaMemcpyAsync(t_cur.data(), b->d_tcur, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     if (rounds) *rounds = r;
     if (patch_updates) *patch_updates = updates;
     int code = 0;
@@ -1169,8 +1215,19 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     cudaFree(b->d_told);
     cudaFree(b->d_tcur);
     cudaFree(b->d_dtp);
-    cudaFree(b->d_list);
     cudaFree(b->d_atiles);
+    cudaFree(b->d_nb_off);
+    cudaFree(b->d_nb_idx);
+    cudaFree(b->d_tfirst);
+    cudaFree(b->d_tcount);
+    cudaFree(b->d_rows_list);
+    cudaFree(b->d_rows_dt);
+    cudaFree(b->d_rows_last);
+    cudaFree(b->d_rows_n);
+    cudaFree(b->d_ntiles);
+    cudaFree(b->d_abort);
+    cudaFree(b->d_ready);
+    cudaFree(b->d_rmax);
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);

@@ -53,13 +53,15 @@ struct PrecisionKernels {
     cudaError_t (*adjoint)(const AdjHostArgs& a, const FillGeom& fg, unsigned* err, cudaStream_t s, int* nlaunch);
     int adj_fields;      // work fields per cell in F and in G
     // asynchronous stepping: guard fill of the listed patches at their own times, and
-    // their own CFL dt (dt_out indexed by patch)
+    // their maximum CFL rate (rate_max indexed by patch: the bits of a non-negative double,
+    // zeroed beforehand).  The list holds nlist entries, or *nlist_dev (<= nlist) when
+    // nlist_dev is not null; grid_y (> 0) caps the blocks along the list
     cudaError_t (*fill_interp)(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list, int nlist,
-                               const int* slice, const double* t_old, const double* t_cur, const FillGeom& fg,
-                               unsigned* err, cudaStream_t s);
+                               const int* nlist_dev, int grid_y, const int* slice, const double* t_old,
+                               const double* t_cur, const FillGeom& fg, unsigned* err, cudaStream_t s);
     cudaError_t (*cfl_patch)(const void* U0, const void* U1, const PatchDev* patches, const int* list, int nlist,
-                             const int* slice, double gamma, double courant, const double dxi[3], const int act[3],
-                             double* dt_out, unsigned* err, cudaStream_t s);
+                             const int* nlist_dev, int grid_y, const int* slice, double gamma, const double dxi[3],
+                             const int act[3], unsigned long long* rate_max, unsigned* err, cudaStream_t s);
     // guard fill + CFL dt in one pass (regular grids: nboff the neighbour table, Zp the padded
     // z extent); partial: npatch * Zp reals; counter: one zeroed unsigned
     cudaError_t (*fill_cfl)(void* U, const PatchDev* patches, int npatch, const int64_t* nboff, int Zp, double gamma,
@@ -79,6 +81,7 @@ struct StepHostArgs {
     const PatchDev* patches;
     const int4* tiles;
     int ntiles;
+    const int* ntiles_dev;   // asynchronous stepping: tile count read on the device (<= ntiles), or null
     int dynamic;
     int* work;
     const double* dt_ptr;

@@ -381,6 +381,7 @@ struct StepArgs {
     const PatchDev* __restrict__ patches;
     const int4* __restrict__ tiles;
     int ntiles;
+    const int* ntiles_dev;  // ASYNC: tile count written by the device scheduler (null: ntiles)
     int dynamic;          // 1: pull tiles from *work (persistent), 0: one tile per CTA
     int* work;            // [0] next tile, [1] finished CTAs
     const double* dt_ptr; // device dt (if not null)
@@ -480,7 +481,11 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
     } else {
         t = blockIdx.x;
     }
-    while (t < a.ntiles) {
+    int ntiles = a.ntiles;
+    if constexpr (ASYNC) {
+        if (a.ntiles_dev) ntiles = min(*a.ntiles_dev, a.ntiles);
+    }
+    while (t < ntiles) {
         const int4 tl = a.tiles[t];
         const PatchDev pt = a.patches[tl.x];
         const R* __restrict__ Uc = a.U;
@@ -674,7 +679,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
             __syncthreads();
             t = s_tile;
         } else {
-            t = a.ntiles;
+            t = ntiles;
         }
     }
     if (a.dynamic && threadIdx.x == 0) {

@@ -64,3 +64,33 @@ def test_async_ragged_bunch_fp64():
     ob = O.Bunch(geom, meta["gamma"])
     err = rel_l1(interior_global(b.download(), geom), interior_global(ob.join(final), geom))
     assert np.all(err <= 1e-11), err
+
+
+def test_async_many_rounds_and_max_rounds_cut():
+    """More rounds than the device scheduler enqueues between two reads of its record (32):
+    the schedule still replays on the oracle across the batch boundaries.  A second run cut
+    short by max_rounds reports MHD_ESTATE and records exactly the first max_rounds rounds
+    of the full run, bitwise."""
+    from paper_2508_09568_gb300 import capi
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, U, meta = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=33, amp=0.9)
+    b, flat, t_span, rounds, updates, log, final, ready_sets, local_dts, t_cur = _run(geom, U, meta["gamma"],
+                                                                                      torch.float64, spans=12.0)
+    assert rounds > 40
+    assert all(t == t_span for t in t_cur)
+    for (plist, dts), rs, ldt in zip(log, ready_sets, local_dts):
+        assert list(plist) == rs
+        assert np.allclose(dts, ldt, rtol=1e-12, atol=0)
+    ob = O.Bunch(geom, meta["gamma"])
+    err = rel_l1(interior_global(b.download(), geom), interior_global(ob.join(final), geom))
+    assert np.all(err <= 1e-11), err
+    cut = rounds - 5
+    b2 = MHDBunch(geom, dtype=torch.float64, gamma=meta["gamma"])
+    b2.upload(flat)
+    with pytest.raises(capi.MHDError) as ei:
+        b2.advance_async(t_span, max_rounds=cut)
+    assert ei.value.code == capi.MHD_ESTATE
+    log2 = b2.async_rounds(cut)
+    for (p1, d1), (p2, d2) in zip(log[:cut], log2):
+        assert np.array_equal(p1, p2)
+        assert np.array_equal(d1, d2)
