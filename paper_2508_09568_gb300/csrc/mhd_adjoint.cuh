@@ -11,7 +11,8 @@
 //
 // Occupancy: the face and edge kernels (the HLLD / 2D-HLL VJPs) are capped at 128
 // registers (two 256-thread blocks per SM) and take their direction from the grid's z
-// index, so each thread handles one face or edge; the cell kernels are capped at 85.
+// index, so each thread handles one face or edge; the slope kernel is capped at 128
+// registers and the other cell kernels at 85.
 //
 // Work arrays (fields of one value per padded cell; index coff[p] + (z*Y + y)*X + x):
 //   W(8) primitives, DW(24) slopes [d][k], FS(6) face-field slopes, EN(3) time-n edge
@@ -383,12 +384,13 @@ __global__ void __launch_bounds__(256, 3) adj_pred(AdjArgs<R> a) {
     const R hdt = R(0.5 * a.dt), gamma = R(a.gamma);
     ADJ_FOR_REGION(a, -1, 1, {
         const int64_t i = C.at(x, y, z);
-        R lo[5];
+        R lo[5], lb[3];
         bool any = false;
         for (int k = 0; k < 5; ++k) {
             lo[k] = fld(a.G, AF_WH + k, a.ncell)[i];
             any |= lo[k] != R(0);
         }
+        for (int c = 0; c < 3; ++c) lb[c] = fld(a.G, AF_WH + 5 + c, a.ncell)[i];   // before any atomic add
         if (any) {
             R q[8], D[3][8], lq[8] = {0, 0, 0, 0, 0, 0, 0, 0}, lD[3][8];
             for (int d = 0; d < 3; ++d)
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(256, 3) adj_pred(AdjArgs<R> a) {
                 for (int k = 0; k < 8; ++k) aadd(&fld(a.G, AF_DW + 8 * d + k, a.ncell)[i], lD[d][k] * R(a.dxi[d]));
         }
         for (int c = 0; c < 3; ++c) {
-            const R l = fld(a.G, AF_WH + 5 + c, a.ncell)[i];
+            const R l = lb[c];
             if (l == R(0)) continue;
             int ox, oy, oz;
             unit(c, ox, oy, oz);
@@ -464,42 +466,63 @@ __global__ void __launch_bounds__(256, 3) adj_en(AdjArgs<R> a) {
 
 // limited slopes of the primitives and of the face fields
 template <typename R>
-__global__ void __launch_bounds__(256, 3) adj_slopes(AdjArgs<R> a) {
+__global__ void __launch_bounds__(256, 2) adj_slopes(AdjArgs<R> a) {
     ADJ_FOR_REGION(a, -1, 2, {
         const int64_t i = C.at(x, y, z);
         const bool inner = x <= pt.gx + pt.nx && y <= pt.gy + pt.ny && z <= pt.gz + pt.nz;
-        for (int d = 0; d < 3; ++d) {
-            int ox, oy, oz;
-            unit(d, ox, oy, oz);
-            const int64_t im = C.at(x - ox, y - oy, z - oz), ip = C.at(x + ox, y + oy, z + oz);
-            if (inner)
+        // Every load of a group is issued before its atomic adds: the fields read here (slope
+        // cotangents, primitives, U) are never written by this kernel, but the compiler
+        // cannot tell them from the accumulated ones and would otherwise wait for each load.
+        if (inner)
+            for (int d = 0; d < 3; ++d) {
+                int ox, oy, oz;
+                unit(d, ox, oy, oz);
+                const int64_t im = C.at(x - ox, y - oy, z - oz), ip = C.at(x + ox, y + oy, z + oz);
+                R l[8], wm[8], w0[8], wp[8];
+#pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const R l = fld(a.G, AF_DW + 8 * d + k, a.ncell)[i];
-                    if (l == R(0)) continue;
                     const R* w = fld(a.F, AF_W + k, a.ncell);
+                    l[k] = fld(a.G, AF_DW + 8 * d + k, a.ncell)[i];
+                    wm[k] = w[im];
+                    w0[k] = w[i];
+                    wp[k] = w[ip];
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (l[k] == R(0)) continue;
                     R lm = 0, l0 = 0, lp = 0;
-                    slope_vjp(w[im], w[i], w[ip], a.limiter, l, lm, l0, lp);
+                    slope_vjp(wm[k], w0[k], wp[k], a.limiter, l[k], lm, l0, lp);
                     R* gw = fld(a.G, AF_W + k, a.ncell);
                     aadd(&gw[im], lm);
                     aadd(&gw[i], l0);
                     aadd(&gw[ip], lp);
                 }
-        }
-        for (int c = 0; c < 3; ++c)
-            for (int kk = 0; kk < 2; ++kk) {
-                const R l = fld(a.G, AF_FS + 2 * c + kk, a.ncell)[i];
-                if (l == R(0)) continue;
-                const int t = (c + kk + 1) % 3;
-                int ox, oy, oz;
-                unit(t, ox, oy, oz);
-                const int64_t im = C.at(x - ox, y - oy, z - oz), ip = C.at(x + ox, y + oy, z + oz);
-                R lm = 0, l0 = 0, lp = 0;
-                slope_vjp(a.U[sidx<R>(pt, C, 5 + c, im)], a.U[sidx<R>(pt, C, 5 + c, i)],
-                          a.U[sidx<R>(pt, C, 5 + c, ip)], a.limiter, l, lm, l0, lp);
-                aadd(&a.lam[sidx<R>(pt, C, 5 + c, im)], lm);
-                aadd(&a.lam[sidx<R>(pt, C, 5 + c, i)], l0);
-                aadd(&a.lam[sidx<R>(pt, C, 5 + c, ip)], lp);
             }
+        R lf[6], um[6], u0[6], up[6];
+        int64_t fim[6], fip[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int c = f >> 1, kk = f & 1;
+            const int t = (c + kk + 1) % 3;
+            int ox, oy, oz;
+            unit(t, ox, oy, oz);
+            fim[f] = C.at(x - ox, y - oy, z - oz);
+            fip[f] = C.at(x + ox, y + oy, z + oz);
+            lf[f] = fld(a.G, AF_FS + f, a.ncell)[i];
+            um[f] = a.U[sidx<R>(pt, C, 5 + c, fim[f])];
+            u0[f] = a.U[sidx<R>(pt, C, 5 + c, i)];
+            up[f] = a.U[sidx<R>(pt, C, 5 + c, fip[f])];
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            if (lf[f] == R(0)) continue;
+            const int c = f >> 1;
+            R lm = 0, l0 = 0, lp = 0;
+            slope_vjp(um[f], u0[f], up[f], a.limiter, lf[f], lm, l0, lp);
+            aadd(&a.lam[sidx<R>(pt, C, 5 + c, fim[f])], lm);
+            aadd(&a.lam[sidx<R>(pt, C, 5 + c, i)], l0);
+            aadd(&a.lam[sidx<R>(pt, C, 5 + c, fip[f])], lp);
+        }
     })
 }
 
@@ -558,10 +581,15 @@ __global__ void adj_fill_transpose(R* lam, const PatchDev* __restrict__ patches,
             const int64_t svol = (int64_t)src.X * src.Y * src.Z;
             R* s = lam + src.off + ((int64_t)sz * src.Y + sy) * src.X + sx;
             R* d = lam + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+            // the ghost's 8 cotangents are loaded before the atomic adds into its source (an
+            // interior cell, never a ghost, so the two never alias)
+            R g[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) g[v] = d[v * vol];
+#pragma unroll
             for (int v = 0; v < 8; ++v) {
-                const R g = d[v * vol];
                 d[v * vol] = R(0);
-                if (g != R(0)) atomicAdd(&s[v * svol], g);
+                if (g[v] != R(0)) atomicAdd(&s[v * svol], g[v]);
             }
         }
     }
@@ -596,10 +624,13 @@ __global__ void adj_fill_transpose_grid(R* lam, const PatchDev* __restrict__ pat
         }
         R* s = lam + neighbour_source(pt, nb, x - gx, y - gy, iz);
         R* d = plane + (int64_t)y * X + x;
+        R g[8];   // loaded before the atomic adds (source interior, destination ghost)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) g[v] = d[v * vol];
+#pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const R g = d[v * vol];
             d[v * vol] = R(0);
-            if (g != R(0)) atomicAdd(&s[v * vol], g);
+            if (g[v] != R(0)) atomicAdd(&s[v * vol], g[v]);
         }
     }
 }
