@@ -209,6 +209,26 @@ int mhd_bunch_advance_host(mhd_bunch *b, void *host_state, int nsteps, double *t
  * mhd_bunch_get_error would. */
 int mhd_bunch_advance_streamed(mhd_bunch *b, void *host_state, int nsteps, int nchunks, double *t_out);
 
+/* Interior layout: the cells a patch owns, without ghost cells.  Patch p starts at element
+ * patch_offsets[p] and is stored as [8][nz][ny][nx], x fastest (variables and face-field
+ * convention of the state layout; nx, ny, nz the patch's cells).  *bytes receives the
+ * size of the whole interior state; patch_offsets (may be NULL) npatch entries. */
+int mhd_bunch_interior_size(const mhd_bunch *b, size_t *bytes, int64_t *patch_offsets);
+
+/* As mhd_bunch_advance_streamed, with the host state in the interior layout
+ * (mhd_bunch_interior_size bytes; page-locked for the copies to overlap): ghost cells are
+ * derived data (the guard fill rebuilds them before every update), so each step moves
+ * only the owned cells, 1/1.675 of the state layout's bytes for 32^3 patches with guard 3.
+ * Per step, chunk k is copied into a library-owned device staging buffer (one interior
+ * state, allocated on first use, released by mhd_bunch_destroy), scattered into the
+ * current state buffer by a copy kernel, and after the update of its patches gathered
+ * from the new state into the staging buffer and copied back into host_interior.  The
+ * results (host_interior, the device state current afterwards, *t_out) equal those of
+ * mhd_bunch_advance_streamed bitwise on the interior.  Same argument rules, errors and
+ * synchronisation as mhd_bunch_advance_streamed. */
+int mhd_bunch_advance_streamed_interior(mhd_bunch *b, void *host_interior, int nsteps, int nchunks,
+                                        double *t_out);
+
 /* Adjoint of one step at fixed dt (the reverse of mhd_bunch_step, including the guard
  * fill): given U^n (interior valid; ghosts are re-filled internally) and the cotangent
  * lam_next of U^{n+1} (interior cells and owned faces), writes

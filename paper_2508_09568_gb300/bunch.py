@@ -155,6 +155,25 @@ class MHDBunch:
                                                        ct.byref(t)))
         return t.value
 
+    def interior_size(self):
+        """(bytes, per-patch element offsets) of the interior layout (mhd_bunch_interior_size)."""
+        nbytes = ct.c_size_t()
+        offs = np.zeros(self.geom.npatch, dtype=np.int64)
+        capi.check(self.lib.mhd_bunch_interior_size(self.h, ct.byref(nbytes), offs.ctypes.data_as(capi.I64P)))
+        return nbytes.value, offs
+
+    def advance_streamed_interior(self, host_interior: torch.Tensor, nsteps: int, nchunks: int = 8) -> float:
+        """As advance_streamed with the host state in the interior layout (owned cells only,
+        per patch [8][nz][ny][nx]; workloads.to_interior builds one); returns the simulated
+        time."""
+        assert host_interior.device.type == "cpu" and host_interior.is_contiguous()
+        assert host_interior.dtype == self.dtype
+        assert host_interior.numel() * self.rb == self.interior_size()[0]
+        t = ct.c_double()
+        capi.check(self.lib.mhd_bunch_advance_streamed_interior(self.h, ct.c_void_p(host_interior.data_ptr()), nsteps,
+                                                                nchunks, ct.byref(t)))
+        return t.value
+
     def advance_async(self, t_span: float, max_rounds: int = 100000):
         """Asynchronous per-patch stepping by t_span (mhd_bunch_advance_async); returns
         (rounds, patch_updates)."""

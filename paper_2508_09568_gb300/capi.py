@@ -53,6 +53,8 @@ SIGNATURES = {
     "mhd_bunch_graph_launch": (I, [P]),
     "mhd_bunch_advance_host": (I, [P, P, I, DP]),
     "mhd_bunch_advance_streamed": (I, [P, P, I, I, DP]),
+    "mhd_bunch_interior_size": (I, [P, ct.POINTER(ct.c_size_t), I64P]),
+    "mhd_bunch_advance_streamed_interior": (I, [P, P, I, I, DP]),
     "mhd_bunch_advance_async": (I, [P, D, I, ct.POINTER(I), I64P]),
     "mhd_bunch_async_round": (I, [P, I, I32P, DP, I, ct.POINTER(I)]),
     "mhd_bunch_step_adjoint": (I, [P, D, P, P, P]),

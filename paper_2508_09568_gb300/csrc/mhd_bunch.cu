@@ -20,6 +20,7 @@
 #include "../../include/mhd_bunch.h"
 #include "mhd_launch.h"
 #include "mhd_sched.cuh"
+#include "mhd_xfer.cuh"
 
 using namespace mhd;
 
@@ -121,6 +122,11 @@ struct mhd_bunch {
     unsigned long long* d_rmax = nullptr;   // maximum CFL rate per patch (double bits)
     std::vector<std::vector<int>> log_patches;
     std::vector<std::vector<double>> log_dts;
+    // interior layout (host transfers of owned cells only): per-patch offsets, device copy
+    // of them, and the device staging buffer of one whole interior state
+    std::vector<int64_t> ioff_h;
+    int64_t* d_ioff = nullptr;
+    void* d_interior = nullptr;
     // host-streamed advance: library-owned copy streams and per-chunk events
     cudaStream_t s_in = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_step, ev_out;
@@ -696,6 +702,17 @@ int mhd_bunch_set_riemann(mhd_bunch* b, int solver) {
     return MHD_OK;
 }
 
+int mhd_bunch_interior_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) {
+    if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
+    int64_t o = 0;
+    for (int p = 0; p < b->npatch; ++p) {
+        if (patch_offsets) patch_offsets[p] = o;
+        o += 8 * (int64_t)b->pn[3 * p] * b->pn[3 * p + 1] * b->pn[3 * p + 2];
+    }
+    *bytes = (size_t)o * b->rb;
+    return MHD_OK;
+}
+
 int mhd_bunch_state_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) {
     if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
     *bytes = b->state_bytes;
@@ -1046,6 +1063,101 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
     return code;
 }
 
+int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int nsteps, int nchunks,
+                                        double* t_out) {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!host_interior || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
+    if (b->stream == nullptr) return fail(MHD_EINVAL, "the bound stream must not be the legacy default stream");
+    const int P = b->npatch;
+    const int K = std::min(nchunks, P);
+    if (nsteps > b->d_dts_cap) {
+        cudaFree(b->d_dts);
+        b->d_dts = nullptr;
+        CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
+        b->d_dts_cap = nsteps;
+    }
+    rc = ensure_stream_pipeline(b, K);
+    if (rc) return rc;
+    size_t ibytes = 0;
+    if (b->ioff_h.empty()) {
+        std::vector<int64_t> io(P);
+        mhd_bunch_interior_size(b, &ibytes, io.data());
+        CK(cudaMalloc(&b->d_ioff, sizeof(int64_t) * P));
+        CK(cudaMemcpy(b->d_ioff, io.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&b->d_interior, ibytes));
+        b->ioff_h = std::move(io);
+    }
+    mhd_bunch_interior_size(b, &ibytes, nullptr);
+    // chunks: contiguous patch ranges of about equal size; interior bytes [bo[k], bo[k+1])
+    std::vector<int> pb(K + 1);
+    std::vector<size_t> bo(K + 1);
+    int maxnz = 1;
+    for (int p = 0; p < P; ++p) maxnz = std::max(maxnz, (int)b->pn[3 * p + 2]);
+    for (int k = 0; k <= K; ++k) {
+        pb[k] = (int)((int64_t)P * k / K);
+        bo[k] = pb[k] < P ? (size_t)b->ioff_h[pb[k]] * b->rb : ibytes;
+    }
+    char* host = static_cast<char*>(host_interior);
+    char* stage = static_cast<char*>(b->d_interior);
+    const int A = b->cur, B = 1 - A;
+    const int wpr = b->rb / 4;
+    auto copy = [&](int k, int buf, int to_padded) -> cudaError_t {
+        const dim3 grid(maxnz, pb[k + 1] - pb[k]);
+        interior_copy_kernel<<<grid, 256, 0, b->stream>>>(static_cast<unsigned*>(b->buf[buf]),
+                                                          static_cast<unsigned*>(b->d_interior), b->d_patches, b->d_ioff,
+                                                          pb[k], pb[k + 1], wpr, to_padded);
+        ++b->launches;
+        return cudaGetLastError();
+    };
+    // the copy streams start after the work already queued on the bound stream
+    CK(cudaEventRecord(b->ev_step[0], b->stream));
+    CK(cudaStreamWaitEvent(b->s_in, b->ev_step[0], 0));
+    CK(cudaStreamWaitEvent(b->s_out, b->ev_step[0], 0));
+    for (int s = 0; s < nsteps; ++s) {
+        // upload chunk k into the staging buffer once the previous step's chunk k is back on
+        // the host (its staging bytes are free then too), and scatter it into the state
+        for (int k = 0; k < K; ++k) {
+            if (s > 0) CK(cudaStreamWaitEvent(b->s_in, b->ev_out[k], 0));
+            CK(cudaMemcpyAsync(stage + bo[k], host + bo[k], bo[k + 1] - bo[k], cudaMemcpyHostToDevice, b->s_in));
+            CK(cudaEventRecord(b->ev_in[k], b->s_in));
+        }
+        for (int k = 0; k < K; ++k) {
+            CK(cudaStreamWaitEvent(b->stream, b->ev_in[k], 0));
+            CK(copy(k, A, 1));
+        }
+        // guard fill and dt need the whole state; the update runs chunk by chunk, each
+        // updated chunk gathered into the staging buffer and sent back to the host
+        b->cur = A;
+        rc = do_fill_cfl(b, b->d_dts + s);
+        for (int k = 0; k < K && !rc; ++k) {
+            rc = do_step_range(b, b->d_dts + s, pb[k], pb[k + 1]);
+            if (rc) break;
+            CK(copy(k, B, 0));
+            CK(cudaEventRecord(b->ev_step[k], b->stream));
+            CK(cudaStreamWaitEvent(b->s_out, b->ev_step[k], 0));
+            CK(cudaMemcpyAsync(host + bo[k], stage + bo[k], bo[k + 1] - bo[k], cudaMemcpyDeviceToHost, b->s_out));
+            CK(cudaEventRecord(b->ev_out[k], b->s_out));
+        }
+        if (rc) {
+            b->cur = A;
+            cudaStreamSynchronize(b->s_in);
+            cudaStreamSynchronize(b->s_out);
+            return rc;
+        }
+    }
+    // join: the bound stream waits for the last downloads; B holds the final state
+    for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(b->stream, b->ev_out[k], 0));
+    b->cur = B;
+    std::vector<double> dts(nsteps);
+    CK(cudaMemcpyAsync(dts.data(), b->d_dts, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, b->stream));
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
+    return code;
+}
+
 int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* rounds, int64_t* patch_updates) {
     int rc = ready(b);
     if (rc) return rc;
@@ -1228,6 +1340,8 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     cudaFree(b->d_abort);
     cudaFree(b->d_ready);
     cudaFree(b->d_rmax);
+    cudaFree(b->d_ioff);
+    cudaFree(b->d_interior);
     cudaFree(b->d_patches);
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);

@@ -92,6 +92,11 @@ class Geometry:
     def interior_cells(self) -> int:
         return int(np.prod(self.patch_n, axis=1).sum())
 
+    def interior_offsets(self) -> np.ndarray:
+        """Element offset of each patch in the interior layout ([8][nz][ny][nx] per patch)."""
+        e = NVAR * np.prod(self.patch_n, axis=1)
+        return np.concatenate([[0], np.cumsum(e)[:-1]]).astype(np.int64)
+
 
 def uniform_geometry(domain, patch, dx=None, bc=None, guard=3, order="xyz") -> Geometry:
     """Box of ``domain`` cells cut into equal patches of ``patch`` cells (x fastest in patch order)."""
@@ -173,6 +178,34 @@ def from_patches(flat: np.ndarray, geom: Geometry, dtype=np.float64) -> np.ndarr
         blk = np.asarray(flat[offs[p]: offs[p] + NVAR * X * Y * Z]).reshape(NVAR, Z, Y, X)
         out[:, o[2]:o[2] + n[2], o[1]:o[1] + n[1], o[0]:o[0] + n[0]] = \
             blk[:, g[2]:g[2] + n[2], g[1]:g[1] + n[1], g[0]:g[0] + n[0]]
+    return out
+
+
+def to_interior(fields, geom: Geometry, dtype=np.float64, out=None) -> np.ndarray:
+    """Cut a global field (array (8, Nz, Ny, Nx) or callable v -> (Nz, Ny, Nx)) into the
+    interior layout: the owned cells of each patch, [8][nz][ny][nx], patches back to back."""
+    offs = geom.interior_offsets()
+    if out is None:
+        out = np.empty(geom.interior_cells() * NVAR, dtype=dtype)
+    for v in range(NVAR):
+        a = fields(v) if callable(fields) else fields[v]
+        for p in range(geom.npatch):
+            n, o = geom.patch_n[p], geom.origin[p]
+            cells = int(np.prod(n))
+            dst = out[offs[p] + v * cells: offs[p] + (v + 1) * cells].reshape(n[2], n[1], n[0])
+            dst[...] = a[o[2]:o[2] + n[2], o[1]:o[1] + n[1], o[0]:o[0] + n[0]]
+    return out
+
+
+def from_interior(flat: np.ndarray, geom: Geometry, dtype=np.float64) -> np.ndarray:
+    """Assemble an interior-layout buffer into a global (8, Nz, Ny, Nx) field."""
+    offs = geom.interior_offsets()
+    N = geom.domain
+    out = np.full((NVAR, N[2], N[1], N[0]), np.nan, dtype=dtype)
+    for p in range(geom.npatch):
+        n, o = geom.patch_n[p], geom.origin[p]
+        blk = np.asarray(flat[offs[p]: offs[p] + NVAR * int(np.prod(n))]).reshape(NVAR, n[2], n[1], n[0])
+        out[:, o[2]:o[2] + n[2], o[1]:o[1] + n[1], o[0]:o[0] + n[0]] = blk
     return out
 
 
