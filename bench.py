@@ -469,8 +469,8 @@ def run_ours(args, ws, rank, local):
         ts = timed(lambda k: [b.advance_host(host, 1) for _ in range(k)], ks)
         e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": ibytes,
                "d2h_bytes_per_step": ibytes, "steps": ke,
-               "path": f"mhd_bunch_advance_streamed_interior, {E2E_CHUNKS} chunks, pinned host state "
-                       "(owned cells only; ghost cells rebuilt on the device)",
+               "path": f"mhd_bunch_advance_streamed_interior, at most {E2E_CHUNKS} chunks cut at whole waves of "
+                       "the update, pinned host state (owned cells only; ghost cells rebuilt on the device)",
                "state_layout": {"value": cells * ke * ws / tp, "steps": ke, "h2d_bytes_per_step": b.nbytes,
                                 "path": f"mhd_bunch_advance_streamed, {E2E_CHUNKS} chunks (ghost cells included)"},
                "serial": {"value": cells * ks * ws / ts, "steps": ks,

@@ -197,7 +197,9 @@ int mhd_bunch_advance_host(mhd_bunch *b, void *host_state, int nsteps, double *t
 /* Host-resident state streamed through the GPU every step (bunches staged from the host
  * for each update and returned, Secs. 2.4 and 4 of the paper), with copies overlapped with
  * the update: the state in host_state (state_size bytes, layout above; page-locked memory
- * for the copies to overlap) is cut into nchunks contiguous runs of patches.  Per step:
+ * for the copies to overlap) is cut into at most nchunks contiguous runs of patches (when
+ * nchunks equal runs would each hold at least one wave of the persistent update, i.e. SM
+ * count x occupancy tiles, the runs are cut at whole waves instead).  Per step:
  * every chunk is copied to the device (on a library-owned stream; chunk k as soon as the
  * previous step returned it), then guard fill -> CFL dt -> the update chunk by chunk on
  * the bound stream, each updated chunk copied back into host_state (on a second library

@@ -449,6 +449,39 @@ int do_step_range(mhd_bunch* b, const double* dt_ptr, int p0, int p1) {
     return MHD_OK;
 }
 
+// Patch ranges of the streamed advances: at most K runs of contiguous patches.  When K
+// equal runs would each hold at least one wave of the persistent update (SM count x
+// occupancy tiles), the runs are cut at whole waves instead, so that no run's launch ends
+// on a partly filled wave; smaller bunches are cut into K runs of about equal patch count.
+int chunk_bounds(mhd_bunch* b, int K, std::vector<int>& pb) {
+    const int P = b->npatch;
+    K = std::max(1, std::min(K, P));
+    pb.assign(1, 0);
+    if (!b->cfg_index.empty()) {
+        const int k = b->config < 0 ? default_config(b) : b->config;
+        const auto& T = b->tiles[k];
+        int occ = 1;
+        CK(step_cfg(b, k).occupancy(&occ));
+        const int64_t wave = (int64_t)b->nsm * std::max(occ, 1);
+        const int64_t per = ((int64_t)T.n + K - 1) / K;
+        if (wave > 0 && per >= wave) {
+            const int64_t target = (per + wave - 1) / wave * wave;
+            int64_t acc = 0;
+            for (int p = 0; p + 1 < P; ++p) {
+                acc += T.count[p];
+                if (acc >= target) {
+                    pb.push_back(p + 1);
+                    acc = 0;
+                }
+            }
+            pb.push_back(P);
+            return MHD_OK;
+        }
+    }
+    for (int c = 1; c <= K; ++c) pb.push_back((int)((int64_t)P * c / K));
+    return MHD_OK;
+}
+
 int ensure_stream_pipeline(mhd_bunch* b, int nchunks) {
     if (!b->s_in) CK(cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking));
     if (!b->s_out) CK(cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking));
@@ -1000,22 +1033,21 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
     if (rc) return rc;
     if (!host_state || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
     if (b->stream == nullptr) return fail(MHD_EINVAL, "the bound stream must not be the legacy default stream");
-    const int K = std::min(nchunks, b->npatch);
     if (nsteps > b->d_dts_cap) {
         cudaFree(b->d_dts);
         b->d_dts = nullptr;
         CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
         b->d_dts_cap = nsteps;
     }
+    // chunks: contiguous patch ranges (chunk_bounds); bytes [bo[k], bo[k+1])
+    std::vector<int> pb;
+    rc = chunk_bounds(b, nchunks, pb);
+    if (rc) return rc;
+    const int K = (int)pb.size() - 1;
     rc = ensure_stream_pipeline(b, K);
     if (rc) return rc;
-    // chunks: contiguous patch ranges of about equal size; bytes [bo[k], bo[k+1])
-    std::vector<int> pb(K + 1);
     std::vector<size_t> bo(K + 1);
-    for (int k = 0; k <= K; ++k) {
-        pb[k] = (int)((int64_t)b->npatch * k / K);
-        bo[k] = pb[k] < b->npatch ? (size_t)b->offs[pb[k]] * b->rb : b->state_bytes;
-    }
+    for (int k = 0; k <= K; ++k) bo[k] = pb[k] < b->npatch ? (size_t)b->offs[pb[k]] * b->rb : b->state_bytes;
     char* host = static_cast<char*>(host_state);
     const int A = b->cur, B = 1 - A;
     char* dA = static_cast<char*>(b->buf[A]);
@@ -1070,13 +1102,16 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
     if (!host_interior || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
     if (b->stream == nullptr) return fail(MHD_EINVAL, "the bound stream must not be the legacy default stream");
     const int P = b->npatch;
-    const int K = std::min(nchunks, P);
     if (nsteps > b->d_dts_cap) {
         cudaFree(b->d_dts);
         b->d_dts = nullptr;
         CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
         b->d_dts_cap = nsteps;
     }
+    std::vector<int> pb;
+    rc = chunk_bounds(b, nchunks, pb);
+    if (rc) return rc;
+    const int K = (int)pb.size() - 1;
     rc = ensure_stream_pipeline(b, K);
     if (rc) return rc;
     size_t ibytes = 0;
@@ -1089,15 +1124,11 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
         b->ioff_h = std::move(io);
     }
     mhd_bunch_interior_size(b, &ibytes, nullptr);
-    // chunks: contiguous patch ranges of about equal size; interior bytes [bo[k], bo[k+1])
-    std::vector<int> pb(K + 1);
+    // chunks (chunk_bounds); interior bytes [bo[k], bo[k+1])
     std::vector<size_t> bo(K + 1);
     int maxnz = 1;
     for (int p = 0; p < P; ++p) maxnz = std::max(maxnz, (int)b->pn[3 * p + 2]);
-    for (int k = 0; k <= K; ++k) {
-        pb[k] = (int)((int64_t)P * k / K);
-        bo[k] = pb[k] < P ? (size_t)b->ioff_h[pb[k]] * b->rb : ibytes;
-    }
+    for (int k = 0; k <= K; ++k) bo[k] = pb[k] < P ? (size_t)b->ioff_h[pb[k]] * b->rb : ibytes;
     char* host = static_cast<char*>(host_interior);
     char* stage = static_cast<char*>(b->d_interior);
     const int A = b->cur, B = 1 - A;

@@ -63,3 +63,25 @@ def test_streamed_interior_equals_state_layout(dtype, case):
         assert np.array_equal(interior_global(b.download(), geom), want)
     code, msg = b.error()
     assert code == 0, msg
+
+
+def test_streamed_chunks_cut_at_whole_waves():
+    """A bunch of 512 one-tile patches: two requested chunks of 256 tiles each hold a wave
+    of the persistent update, so the runs are cut at whole waves; the results stay bitwise
+    those of the device-resident steps, in both host layouts."""
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, U, meta = W.small_box(ncell=(64, 64, 64), patch=(8, 8, 8), seed=34)
+    flat = rounded(W.to_patches(U, geom), torch.float32)
+    b = MHDBunch(geom, dtype=torch.float32, gamma=meta["gamma"])
+    ref = torch.tensor(flat.astype(np.float32)).pin_memory()
+    t_ref = b.advance_host(ref, 2)
+    want = interior_global(ref.numpy(), geom)
+    for nchunks in (2, 3, 4):
+        host = torch.tensor(flat.astype(np.float32)).pin_memory()
+        assert b.advance_streamed(host, 2, nchunks) == t_ref
+        assert np.array_equal(interior_global(host.numpy(), geom), want)
+        hi = torch.tensor(W.to_interior(U, geom, dtype=np.float32)).pin_memory()
+        assert b.advance_streamed_interior(hi, 2, nchunks) == t_ref
+        assert np.array_equal(W.from_interior(hi.numpy().astype(np.float64), geom), want)
+    code, msg = b.error()
+    assert code == 0, msg
