@@ -246,6 +246,37 @@ def async_leg(b, host, geom, spans=4):
             "time_ratio_async_over_sync": ta / ts}
 
 
+def e2e_leg(b, host, host_int, cells, ws, ke):
+    """End to end through the C ABI on host buffers: the host-resident state streamed
+    through the GPU every step (mhd_bunch_advance_streamed_interior: the owned cells of at
+    most E2E_CHUNKS chunks uploaded, updated and downloaded, overlapped; every step copies
+    the whole interior state to the device and back), beside the state-layout stream and
+    one serial call per step (copy in, fill, dt, step, copy out)."""
+    ibytes = b.interior_size()[0]
+
+    def timed(call, k):
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        call(k)
+        return allmax(time.perf_counter() - t0, ws)
+
+    b.advance_streamed_interior(host_int, 1, E2E_CHUNKS)
+    te = timed(lambda k: b.advance_streamed_interior(host_int, k, E2E_CHUNKS), ke)
+    b.advance_streamed(host, 1, E2E_CHUNKS)
+    tp = timed(lambda k: b.advance_streamed(host, k, E2E_CHUNKS), ke)
+    ks = 2
+    ts = timed(lambda k: [b.advance_host(host, 1) for _ in range(k)], ks)
+    return {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": ibytes,
+            "d2h_bytes_per_step": ibytes, "steps": ke,
+            "path": f"mhd_bunch_advance_streamed_interior, at most {E2E_CHUNKS} chunks cut at whole waves of "
+                    "the update, pinned host state (owned cells only; ghost cells rebuilt on the device)",
+            "state_layout": {"value": cells * ke * ws / tp, "steps": ke, "h2d_bytes_per_step": b.nbytes,
+                             "path": f"mhd_bunch_advance_streamed, {E2E_CHUNKS} chunks (ghost cells included)"},
+            "serial": {"value": cells * ks * ws / ts, "steps": ks,
+                       "path": "mhd_bunch_advance_host one step per call: H2D, fill, dt, step, D2H"}}
+
+
 def adjoint_leg(dev, dtype, rollout_steps=200, ckpt=10, reps=5):
     """Adjoint / forward time on the adjoint workload (64^3 = 8 x 32^3, fixed dt): one step
     (fill + update) against one adjoint step, and a checkpointed rollout's backward against
@@ -349,7 +380,7 @@ def run_ours(args, ws, rank, local):
     host = torch.empty(geom.state_elems(), dtype=dtype).pin_memory()
     W.to_patches(fields, geom, dtype=np.float32 if rb == 4 else np.float64, out=host.numpy())
     host_int = None
-    if not args.no_e2e and args.leg is None:
+    if not args.no_e2e and args.leg in (None, "e2e"):
         # the same state in the interior layout (owned cells only) for the end-to-end leg
         host_int = torch.empty(geom.interior_cells() * 8, dtype=dtype).pin_memory()
         W.to_interior(fields, geom, dtype=np.float32 if rb == 4 else np.float64, out=host_int.numpy())
@@ -364,6 +395,12 @@ def run_ours(args, ws, rank, local):
     if args.leg == "async":
         if rank == 0:
             print(json.dumps({"leg": "async", **async_leg(b, host, geom)}), flush=True)
+        b.close()
+        return
+    if args.leg == "e2e":
+        rec = e2e_leg(b, host, host_int, geom.interior_cells(), ws, max(2, min(args.steps, 10)))
+        if rank == 0:
+            print(json.dumps({"leg": "e2e", **rec}), flush=True)
         b.close()
         return
     if args.config >= 0:
@@ -443,38 +480,7 @@ def run_ours(args, ws, rank, local):
     async_rec = async_leg(b, host, geom) if rank == 0 and not args.no_extra else None
 
     # ---- end to end through the C ABI on host buffers (H2D + fill + dt + step + D2H per step)
-    e2e = None
-    if not args.no_e2e:
-        # host-resident state streamed through the GPU every step
-        # (mhd_bunch_advance_streamed_interior: the owned cells of E2E_CHUNKS chunks uploaded,
-        # updated and downloaded, overlapped); every step copies the whole interior state to
-        # the device and back
-        ke = max(2, min(args.steps, 10))
-        ibytes = b.interior_size()[0]
-
-        def timed(call, k):
-            torch.cuda.synchronize()
-            barrier(ws)
-            t0 = time.perf_counter()
-            call(k)
-            return allmax(time.perf_counter() - t0, ws)
-
-        b.advance_streamed_interior(host_int, 1, E2E_CHUNKS)
-        te = timed(lambda k: b.advance_streamed_interior(host_int, k, E2E_CHUNKS), ke)
-        # the state layout (ghost cells cross the link too), and the same without overlap,
-        # one call per step (copy in, fill, dt, step, copy out)
-        b.advance_streamed(host, 1, E2E_CHUNKS)
-        tp = timed(lambda k: b.advance_streamed(host, k, E2E_CHUNKS), ke)
-        ks = 2
-        ts = timed(lambda k: [b.advance_host(host, 1) for _ in range(k)], ks)
-        e2e = {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": ibytes,
-               "d2h_bytes_per_step": ibytes, "steps": ke,
-               "path": f"mhd_bunch_advance_streamed_interior, at most {E2E_CHUNKS} chunks cut at whole waves of "
-                       "the update, pinned host state (owned cells only; ghost cells rebuilt on the device)",
-               "state_layout": {"value": cells * ke * ws / tp, "steps": ke, "h2d_bytes_per_step": b.nbytes,
-                                "path": f"mhd_bunch_advance_streamed, {E2E_CHUNKS} chunks (ghost cells included)"},
-               "serial": {"value": cells * ks * ws / ts, "steps": ks,
-                          "path": "mhd_bunch_advance_host one step per call: H2D, fill, dt, step, D2H"}}
+    e2e = None if args.no_e2e else e2e_leg(b, host, host_int, cells, ws, max(2, min(args.steps, 10)))
 
     # ---- roofline of the dominant kernel (the fused step): SIMT-arithmetic bound; the
     # peak is the FMA rate the library's probe kernel measures on this GPU
@@ -538,7 +544,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--config", type=int, default=-1, help="tile configuration (default: autotune)")
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged-box and adjoint legs")
-    ap.add_argument("--leg", default=None, choices=["async", "ragged", "adjoint"],
+    ap.add_argument("--leg", default=None, choices=["async", "ragged", "adjoint", "e2e"],
                     help="run only this secondary leg and print its record (for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

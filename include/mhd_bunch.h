@@ -227,7 +227,8 @@ int mhd_bunch_interior_size(const mhd_bunch *b, size_t *bytes, int64_t *patch_of
  * from the new state into the staging buffer and copied back into host_interior.  The
  * results (host_interior, the device state current afterwards, *t_out) equal those of
  * mhd_bunch_advance_streamed bitwise on the interior.  Same argument rules, errors and
- * synchronisation as mhd_bunch_advance_streamed. */
+ * synchronisation as mhd_bunch_advance_streamed; MHD_EINVAL as well if a padded patch
+ * holds 2^31 or more 4-byte words. */
 int mhd_bunch_advance_streamed_interior(mhd_bunch *b, void *host_interior, int nsteps, int nchunks,
                                         double *t_out);
 

@@ -1108,6 +1108,9 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
         CK(cudaMalloc(&b->d_dts, sizeof(double) * nsteps));
         b->d_dts_cap = nsteps;
     }
+    for (const auto& q : b->hp)   // the copy kernel indexes within a patch in 32 bits
+        if ((int64_t)8 * q.X * q.Y * q.Z * (b->rb / 4) >= ((int64_t)1 << 31))
+            return fail(MHD_EINVAL, "a patch is too large for the interior-layout stream (2^31 words)");
     std::vector<int> pb;
     rc = chunk_bounds(b, nchunks, pb);
     if (rc) return rc;
