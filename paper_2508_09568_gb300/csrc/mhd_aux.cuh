@@ -192,19 +192,29 @@ struct CflArgs {
 // CFL rate of the interior cell c (pointer to its rho) of a patch: sum over active axes of
 // (|u_d| + c_f,d) / dx_d, with the cell-centred field the mean of the cell's two faces
 // (the same with the cell's three high faces given)
+// (from the cell's 8 values u)
 template <typename R>
-__device__ __forceinline__ R cell_rate_faces(const R* c, int64_t vol, R bxh, R byh, R bzh, bool act1, bool act2,
-                                             R gamma, R gm1, R dxi0, R dxi1, R dxi2) {
-    const R bxc = R(0.5) * (c[5 * vol] + bxh);
-    const R byc = act1 ? R(0.5) * (c[6 * vol] + byh) : c[6 * vol];
-    const R bzc = act2 ? R(0.5) * (c[7 * vol] + bzh) : c[7 * vol];
+__device__ __forceinline__ R cell_rate_vals(const R u[8], R bxh, R byh, R bzh, bool act1, bool act2, R gamma,
+                                            R gm1, R dxi0, R dxi1, R dxi2) {
+    const R bxc = R(0.5) * (u[5] + bxh);
+    const R byc = act1 ? R(0.5) * (u[6] + byh) : u[6];
+    const R bzc = act2 ? R(0.5) * (u[7] + bzh) : u[7];
     R q[8];
-    cons_to_prim(c[0], c[vol], c[2 * vol], c[3 * vol], c[4 * vol], bxc, byc, bzc, gm1, q);
+    cons_to_prim(u[0], u[1], u[2], u[3], u[4], bxc, byc, bzc, gm1, q);
     const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
     R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
     if (act1) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
     if (act2) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;
     return rate;
+}
+
+template <typename R>
+__device__ __forceinline__ R cell_rate_faces(const R* c, int64_t vol, R bxh, R byh, R bzh, bool act1, bool act2,
+                                             R gamma, R gm1, R dxi0, R dxi1, R dxi2) {
+    R u[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) u[v] = c[v * vol];
+    return cell_rate_vals(u, bxh, byh, bzh, act1, act2, gamma, gm1, dxi0, dxi1, dxi2);
 }
 
 template <typename R>
@@ -338,18 +348,31 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
         const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
         const bool top = iz + 1 == pt.nz;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int yy = wid; yy < pt.ny; yy += nw) {
-            const R* row = plane + (int64_t)(yy + gy) * X + gx;
+        // each warp takes RR rows at a time, every load of the RR cells before the rates
+        constexpr int RR = 4;
+        for (int y0 = wid * RR; y0 < pt.ny; y0 += nw * RR) {
             for (int x = lane; x < pt.nx; x += 32) {
-                const R* c = row + x;
-                const R bxh = c[5 * vol + 1];
-                const R byh = act1 ? c[6 * vol + X] : R(0);
-                R bzh = R(0);
-                if (act2) bzh = top ? U[7 * vol + neighbour_source(pt, nb, x, yy, pt.nz)] : c[7 * vol + (int64_t)X * Y];
-                const R rate = cell_rate_faces(c, vol, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1,
-                                               dxi2);
-                if (!isfinite((double)rate)) bad = true;
-                else vmax = rate > vmax ? rate : vmax;
+                R u[RR][8], bxh[RR], byh[RR], bzh[RR];
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int yy = min(y0 + r, pt.ny - 1);
+                    const R* c = plane + (int64_t)(yy + gy) * X + gx + x;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) u[r][v] = c[v * vol];
+                    bxh[r] = c[5 * vol + 1];
+                    byh[r] = act1 ? c[6 * vol + X] : R(0);
+                    bzh[r] = R(0);
+                    if (act2)
+                        bzh[r] = top ? U[7 * vol + neighbour_source(pt, nb, x, yy, pt.nz)] : c[7 * vol + (int64_t)X * Y];
+                }
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    if (y0 + r >= pt.ny) continue;
+                    const R rate = cell_rate_vals(u[r], bxh[r], byh[r], bzh[r], act1 != 0, act2 != 0, gamma, gm1, dxi0,
+                                                  dxi1, dxi2);
+                    if (!isfinite((double)rate)) bad = true;
+                    else vmax = rate > vmax ? rate : vmax;
+                }
             }
         }
     }
