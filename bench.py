@@ -525,6 +525,15 @@ def run_ours(args, ws, rank, local):
                                         "f32": adjoint_leg(dev, torch.float32)}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(8)
+        # one host core: ns per cell-update, the per-core kind of figure the paper quotes
+        nt = torch.get_num_threads()
+        torch.set_num_threads(1)
+        try:
+            one = cpu_baseline(2)
+        finally:
+            torch.set_num_threads(nt)
+        out["cpu_baseline"]["single_core"] = {"ns_per_cell_update": 1e9 / one["value"], "cores": 1,
+                                              "sample": one["sample"]}
     b.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -94,3 +94,24 @@ def test_async_many_rounds_and_max_rounds_cut():
     for (p1, d1), (p2, d2) in zip(log[:cut], log2):
         assert np.array_equal(p1, p2)
         assert np.array_equal(d1, d2)
+
+
+def test_async_nonphysical_state_is_reported():
+    """Failure detection without a GPU fault: a patch whose every density is negative has no
+    finite CFL rate, so its dt is not finite; the device scheduler sets that dt to 0 and
+    schedules no further round, and the call returns MHD_EPHYS after one round."""
+    from paper_2508_09568_gb300 import capi
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, U, meta = W.small_box(ncell=(16, 16, 16), patch=(8, 8, 8), seed=1)
+    U = U.copy()
+    U[0, 0:8, 0:8, 0:8] = -1.0        # every cell of the patch at the origin
+    b = MHDBunch(geom, dtype=torch.float64, gamma=meta["gamma"])
+    b.upload(W.to_patches(U, geom))
+    with pytest.raises(capi.MHDError) as ei:
+        b.advance_async(1e-2)
+    assert ei.value.code == capi.MHD_EPHYS
+    assert len(b.async_rounds(1)[0][0]) == geom.npatch   # round 0: every patch (all at t = 0)
+    with pytest.raises(capi.MHDError):                     # and no round after it
+        b.async_rounds(2)
+    code, msg = b.error()
+    assert code == 0, msg          # the error word was read (and cleared) by the call
