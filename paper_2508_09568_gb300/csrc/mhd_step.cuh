@@ -451,7 +451,8 @@ __device__ __forceinline__ void stage_update(const StepSmem<R, C>& S, const R* _
 
 // PREFETCH (3D): the raw plane m+1 is copied with cp.async into the W-ring slot of plane
 // c-1 (free once plane c is prepared) while the flux stage of plane c runs, instead of
-// being loaded at the start of the next iteration.
+// being loaded at the start of the next iteration; its conversion then shares the phase of
+// the update, so a plane takes three barriers (update + convert / prep / flux).
 // ASYNC: asynchronous stepping (a.slice, a.dt_patch): per-tile slice choice and dt; a
 // separate instantiation so that the synchronous step keeps its kernel-wide constants.
 template <typename R, int NDIM, int TX, int TY, int NT, int MINB, bool PREFETCH, bool ASYNC>
@@ -524,13 +525,23 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
             // ---- load plane m (+ the update of plane s-5, which reads only flux buffers);
             // with the prefetch, plane m was issued in the previous iteration's flux stage
             R* Wm_slot = S.W(C::AZ ? (m + 3) % 3 : 0);
-            if ((!PF || s == 0) && (!C::AZ || m <= nz + 1))
-                stage_load<R, C, PF>(Uc, pt, x0, y0, m, Wm_slot, bznext);
+            if constexpr (PF) {
+                // plane m arrived under the previous iteration's flux stage (waited for and
+                // published by its closing barrier); only the first plane is loaded here
+                if (s == 0) {
+                    stage_load<R, C, true>(Uc, pt, x0, y0, m, Wm_slot, bznext);
+                    cp_async_wait_all();
+                    __syncthreads();
+                }
+            } else if (!C::AZ || m <= nz + 1) {
+                stage_load<R, C, false>(Uc, pt, x0, y0, m, Wm_slot, bznext);
+            }
             if (C::AZ && s >= 5)
                 stage_update<R, C>(S, Uc, Un, pt, x0, y0, s - 5, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
-            if (PF) cp_async_wait_all();
-            __syncthreads();
+            if constexpr (!PF) __syncthreads();
             if (C::AZ && m > nz + 1) break;      // the last update is done
+            // PREFETCH: the conversion shares the update's phase (the update reads only the
+            // flux buffers and U^n, the conversion only its ring slot and bznext)
             stage_convert<R, C>(Wm_slot, bznext, gm1);
             __syncthreads();
             // ---- prep plane c: threads walk rows of the W-ring pitch LX so that the
@@ -667,6 +678,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs<R> a) {
                     }
                 }
             }
+            if (PF) cp_async_wait_all();   // plane m+1, published by the barrier below
             __syncthreads();
             if (!C::AZ) {
                 stage_update<R, C>(S, Uc, Un, pt, x0, y0, 0, wx, wy, dtdx0, dtdx1, dtdx2, a.err);
