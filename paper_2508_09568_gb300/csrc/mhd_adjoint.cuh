@@ -369,10 +369,13 @@ __global__ void __launch_bounds__(256, 2) adj_edges(AdjArgs<R> a) {
             const int cz[4] = {z - az - bz, z - bz, z - az, z};
             const int sa[4] = {1, -1, 1, -1}, sb[4] = {1, 1, -1, -1};
             Corner<R> s[4];
+#pragma unroll
             for (int k = 0; k < 4; ++k) s[k] = adj_corner(a, C, e, cx[k], cy[k], cz[k], sa[k], sb[k], fa[k], fb[k]);
             Corner<R> g[4];
+#pragma unroll
             for (int k = 0; k < 4; ++k) g[k] = Corner<R>{0, 0, 0, 0, 0, 0, 0};
             emf2d_vjp(s[0], s[1], s[2], s[3], gamma, lE, g[0], g[1], g[2], g[3]);
+#pragma unroll
             for (int k = 0; k < 4; ++k) adj_corner_scatter(a, C, e, cx[k], cy[k], cz[k], sa[k], sb[k], fa[k], fb[k], g[k]);
         }
     })

@@ -705,22 +705,27 @@ MHD_HD void emf2d_vjp(const Corner<R>& SW, const Corner<R>& SE, const Corner<R>&
         gs[k]->Ba -= g_e[k] * st[k]->ub;
     }
     // speeds -> corner velocities and fast speeds
+    // (each corner tests whether it was selected, so that every index is a compile-time
+    // constant and the corner cotangents stay in registers)
     R g_cfa[4] = {0, 0, 0, 0}, g_cfb[4] = {0, 0, 0, 0};
-    if (kE >= 0) {
-        gs[kE]->ua += g_sE;
-        g_cfa[kE] += g_sE;
-    }
-    if (kW >= 0) {
-        gs[kW]->ua += g_sW;
-        g_cfa[kW] -= g_sW;
-    }
-    if (kN >= 0) {
-        gs[kN]->ub += g_sN;
-        g_cfb[kN] += g_sN;
-    }
-    if (kS >= 0) {
-        gs[kS]->ub += g_sS;
-        g_cfb[kS] -= g_sS;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k == kE) {
+            gs[k]->ua += g_sE;
+            g_cfa[k] += g_sE;
+        }
+        if (k == kW) {
+            gs[k]->ua += g_sW;
+            g_cfa[k] -= g_sW;
+        }
+        if (k == kN) {
+            gs[k]->ub += g_sN;
+            g_cfb[k] += g_sN;
+        }
+        if (k == kS) {
+            gs[k]->ub += g_sS;
+            g_cfb[k] -= g_sS;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
