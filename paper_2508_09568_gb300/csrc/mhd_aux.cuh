@@ -61,28 +61,55 @@ __device__ __forceinline__ int wrap_axis(int g, int N, int lo, int hi) {
 template <typename R>
 __global__ void fill_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches, int npatch,
                             FillGeom fg, unsigned* err) {
+    // four ghost cells per thread and pass: their owner lookups and loads all in flight
+    // before the stores
+    constexpr int NC = 4;
     for (int p = blockIdx.y; p < npatch; p += gridDim.y) {
         const PatchDev pt = patches[p];
         const int ng = ghost_count(pt);
         const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
-            int x, y, z;
-            ghost_coord(pt, k, x, y, z);
-            const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
-            const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
-            const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
-            const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
-            if (ow < 0 || ow >= npatch) {
-                atomicOr(err, ERR_BOUNDS);
-                continue;
-            }
-            const PatchDev src = patches[ow];
-            const int sx = gxg - src.ox + src.gx, sy = gyg - src.oy + src.gy, sz = gzg - src.oz + src.gz;
-            const int64_t svol = (int64_t)src.X * src.Y * src.Z;
-            const R* s = U + src.off + ((int64_t)sz * src.Y + sy) * src.X + sx;
-            R* d = U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+        const int stride = gridDim.x * blockDim.x;
+        for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < ng; k0 += NC * stride) {
+            const R* s[NC];
+            R* d[NC];
+            int64_t svol[NC];
+            bool on[NC];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) d[v * vol] = s[v * svol];
+            for (int c = 0; c < NC; ++c) {
+                const int k = k0 + c * stride;
+                on[c] = k < ng;
+                s[c] = U;
+                d[c] = U;
+                svol[c] = 0;
+                if (!on[c]) continue;
+                int x, y, z;
+                ghost_coord(pt, k, x, y, z);
+                const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
+                const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
+                const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
+                const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
+                if (ow < 0 || ow >= npatch) {
+                    atomicOr(err, ERR_BOUNDS);
+                    on[c] = false;
+                    continue;
+                }
+                const PatchDev src = patches[ow];
+                const int sx = gxg - src.ox + src.gx, sy = gyg - src.oy + src.gy, sz = gzg - src.oz + src.gz;
+                svol[c] = (int64_t)src.X * src.Y * src.Z;
+                s[c] = U + src.off + ((int64_t)sz * src.Y + sy) * src.X + sx;
+                d[c] = U + pt.off + ((int64_t)z * pt.Y + y) * pt.X + x;
+            }
+            R v[NC][8];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[c][q] = on[c] ? s[c][q * svol[c]] : R(0);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (on[c]) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) d[c][q * vol] = v[c][q];
+                }
         }
     }
 }
@@ -422,38 +449,64 @@ __global__ void fill_interp_kernel(R* __restrict__ U0, R* __restrict__ U1, const
         const int64_t vol = (int64_t)pt.X * pt.Y * pt.Z;
         R* Up = (slice[p] ? U1 : U0) + pt.off;
         const double tp = t_cur[p];
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
-            int x, y, z;
-            ghost_coord(pt, k, x, y, z);
-            const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
-            const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
-            const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
-            const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
-            if (ow < 0 || ow >= npatch) {
-                atomicOr(err, ERR_BOUNDS);
-                continue;
+        // two ghost cells per thread and pass, both slices of both sources loaded before
+        // the stores
+        constexpr int NC = 2;
+        const int stride = gridDim.x * blockDim.x;
+        for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < ng; k0 += NC * stride) {
+            const R* cur[NC];
+            const R* old[NC];
+            R* d[NC];
+            int64_t svol[NC];
+            double w[NC];
+            bool on[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int k = k0 + c * stride;
+                on[c] = k < ng;
+                cur[c] = old[c] = U0;
+                d[c] = Up;
+                svol[c] = 0;
+                w[c] = 1.0;
+                if (!on[c]) continue;
+                int x, y, z;
+                ghost_coord(pt, k, x, y, z);
+                const int gxg = wrap_axis(pt.ox + x - pt.gx, fg.N[0], fg.bc[0][0], fg.bc[0][1]);
+                const int gyg = wrap_axis(pt.oy + y - pt.gy, fg.N[1], fg.bc[1][0], fg.bc[1][1]);
+                const int gzg = wrap_axis(pt.oz + z - pt.gz, fg.N[2], fg.bc[2][0], fg.bc[2][1]);
+                const int ow = fg.owner[((gzg / fg.bs[2]) * fg.M[1] + gyg / fg.bs[1]) * fg.M[0] + gxg / fg.bs[0]];
+                if (ow < 0 || ow >= npatch) {
+                    atomicOr(err, ERR_BOUNDS);
+                    on[c] = false;
+                    continue;
+                }
+                const PatchDev src = patches[ow];
+                const int64_t so = src.off +
+                                   ((int64_t)(gzg - src.oz + src.gz) * src.Y + (gyg - src.oy + src.gy)) * src.X +
+                                   (gxg - src.ox + src.gx);
+                svol[c] = (int64_t)src.X * src.Y * src.Z;
+                cur[c] = (slice[ow] ? U1 : U0) + so;
+                old[c] = (slice[ow] ? U0 : U1) + so;
+                const double den = t_cur[ow] - t_old[ow];
+                w[c] = den > 0.0 ? (tp - t_old[ow]) / den : 1.0;
+                d[c] = Up + ((int64_t)z * pt.Y + y) * pt.X + x;
             }
-            const PatchDev src = patches[ow];
-            const int64_t so = src.off + ((int64_t)(gzg - src.oz + src.gz) * src.Y + (gyg - src.oy + src.gy)) * src.X +
-                               (gxg - src.ox + src.gx);
-            const int64_t svol = (int64_t)src.X * src.Y * src.Z;
-            const R* cur = (slice[ow] ? U1 : U0) + so;
-            const R* old = (slice[ow] ? U0 : U1) + so;
-            const double den = t_cur[ow] - t_old[ow];
-            const double w = den > 0.0 ? (tp - t_old[ow]) / den : 1.0;
-            R* d = Up + ((int64_t)z * pt.Y + y) * pt.X + x;
-            if (w >= 1.0) {
+            R vc[NC][8], vo[NC][8];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) d[v * vol] = cur[v * svol];
-            } else if (w <= 0.0) {
+            for (int c = 0; c < NC; ++c)
 #pragma unroll
-                for (int v = 0; v < 8; ++v) d[v * vol] = old[v * svol];
-            } else {
-                const R wr = R(w);
+                for (int q = 0; q < 8; ++q) {
+                    vc[c][q] = on[c] ? cur[c][q * svol[c]] : R(0);
+                    vo[c][q] = on[c] ? old[c][q * svol[c]] : R(0);
+                }
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const R o = old[v * svol];
-                    d[v * vol] = o + wr * (cur[v * svol] - o);
+            for (int c = 0; c < NC; ++c) {
+                if (!on[c]) continue;
+                const R wr = R(w[c]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const R o = vo[c][q];
+                    d[c][q * vol] = w[c] >= 1.0 ? vc[c][q] : (w[c] <= 0.0 ? o : o + wr * (vc[c][q] - o));
                 }
             }
         }
