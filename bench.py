@@ -38,11 +38,13 @@ BYTES_PER_CELL = {4: 64.0, 8: 128.0}       # read 8 values + write 8 values per 
 SMS, FP32_LANES = 152, 128                 # GB300: SMs, FP32 lanes per SM
 E2E_CHUNKS = 32                            # chunks of the host-streamed end-to-end leg
 # DRAM bytes (read + write) per cell-update of the fused step kernel, FP32, 32^3 patches,
-# 32 x 8 tiles of 512 threads: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of a 192^3 box of the same patches and tiles (452.17 MB + 233.64 MB for
-# 7,077,888 cells).  Traffic scales with the number of patches, so a launch on the full
-# box moves this many bytes per cell.  Valid for this kernel version only.
-STEP_DRAM_BYTES_PER_CELL = {(4, 32, (32, 8, 512)): (452.174848e6 + 233.639424e6) / 7077888}
+# per tile configuration (the two the autotuner picks between on this machine):
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a 192^3 box of the
+# same patches and tiles (7,077,888 cells; 32 x 8: 452.17 MB + 233.64 MB, 16 x 16:
+# 453.77 MB + 235.35 MB).  Traffic scales with the number of patches, so a launch on the
+# full box moves this many bytes per cell.  Valid for this kernel version only.
+STEP_DRAM_BYTES_PER_CELL = {(4, 32, (32, 8, 512)): (452.174848e6 + 233.639424e6) / 7077888,
+                            (4, 32, (16, 16, 512)): (453.769216e6 + 235.346688e6) / 7077888}
 
 
 def peaks():
