@@ -63,8 +63,14 @@ enum { MHD_RIEMANN_HLLD = 0, MHD_RIEMANN_HLL = 1 };
  *   PER_PATCH  : one launch per patch (the plain path),
  *   BUNCHED    : one launch over every tile of every patch,
  *   PERSISTENT : one launch of (SM count x resident CTAs) CTAs that pull tiles from a
- *                device work counter until the bunch is done.                          */
-enum { MHD_MODE_PER_PATCH = 0, MHD_MODE_BUNCHED = 1, MHD_MODE_PERSISTENT = 2 };
+ *                device work counter until the bunch is done,
+ *   MIXED      : for bunches of several patch sizes: each patch-size class takes its own
+ *                tile configuration (chosen per class by mhd_bunch_autotune) and the
+ *                update is one persistent launch per configuration in use, over the
+ *                tiles of its patches; until mhd_bunch_autotune has run in this mode, as
+ *                PERSISTENT.  The streamed and asynchronous advances use the single
+ *                configuration of mhd_bunch_set_mode in every mode.                     */
+enum { MHD_MODE_PER_PATCH = 0, MHD_MODE_BUNCHED = 1, MHD_MODE_PERSISTENT = 2, MHD_MODE_MIXED = 3 };
 
 /* Create a bunch of npatch equal patches of nx*ny*nz active cells.
  * guard: ghost width on active axes; must be >= 3 (the update reads two ghost cells
@@ -176,7 +182,10 @@ int mhd_bunch_config_info(const mhd_bunch *b, int config, int *tile_x, int *tile
 
 /* Time each tile configuration on the bound state (a few steps each, the state is
  * restored afterwards) and keep the fastest.  If cache_path is not NULL the choice is
- * read from / written to that text file, keyed by device, precision and patch sizes. */
+ * read from / written to that text file, keyed by device, precision and patch sizes.
+ * In MHD_MODE_MIXED every patch-size class is timed with every configuration on its own
+ * tiles and takes its fastest (cache_path is not used); *chosen receives the
+ * configuration of the class holding the most cells. */
 int mhd_bunch_autotune(mhd_bunch *b, const char *cache_path, int *chosen);
 
 /* Capture nsteps of (fill guards -> CFL dt on the device (mhd_bunch_fill_cfl_device) ->

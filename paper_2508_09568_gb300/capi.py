@@ -16,7 +16,7 @@ MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_EPHYS, MHD_EBOUNDS, MHD_ETIMEOUT,
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_LIMITER_MINMOD, MHD_LIMITER_MC = 0, 1
 MHD_RIEMANN_HLLD, MHD_RIEMANN_HLL = 0, 1
-MHD_MODE_PER_PATCH, MHD_MODE_BUNCHED, MHD_MODE_PERSISTENT = 0, 1, 2
+MHD_MODE_PER_PATCH, MHD_MODE_BUNCHED, MHD_MODE_PERSISTENT, MHD_MODE_MIXED = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA", -4: "MHD_EPHYS",
                 -5: "MHD_EBOUNDS", -6: "MHD_ETIMEOUT", -7: "MHD_ESTATE"}

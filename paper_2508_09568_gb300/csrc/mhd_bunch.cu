@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -131,6 +132,13 @@ struct mhd_bunch {
     cudaStream_t s_in = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in, ev_step, ev_out;
     int mode = MHD_MODE_PERSISTENT, config = -1;
+    // MHD_MODE_MIXED: per configuration, the tiles (longest first) of the patches whose
+    // size class was assigned that configuration by the autotuner (empty: not assigned)
+    struct MixedTiles {
+        int4* d_tiles = nullptr;
+        int n = 0;
+    };
+    std::vector<MixedTiles> mixed;
     // captured step sequences; with an odd step count the second starts from the other buffer
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -151,12 +159,18 @@ int default_config(const mhd_bunch* b) {
 
 const StepLaunch& step_cfg(const mhd_bunch* b, int k) { return b->K->step[b->cfg_index[k]]; }
 
+void free_mixed(mhd_bunch* b) {
+    for (auto& m : b->mixed) cudaFree(m.d_tiles);
+    b->mixed.clear();
+}
+
 void free_tiles(mhd_bunch* b) {
     for (auto& t : b->tiles) {
         cudaFree(t.d_nat);
         cudaFree(t.d_lpt);
     }
     b->tiles.clear();
+    free_mixed(b);
 }
 
 void release_graph(mhd_bunch* b) {
@@ -413,6 +427,22 @@ int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
         a.dynamic = 0;
         CK(L.launch(&a, T.n, b->stream));
         b->launches++;
+    } else if (b->mode == MHD_MODE_MIXED && !b->mixed.empty()) {
+        // one persistent launch per configuration in use (each resets the work counter
+        // when its last CTA finishes, so the next one starts from zero)
+        for (size_t c = 0; c < b->mixed.size(); ++c) {
+            const auto& M = b->mixed[c];
+            if (M.n == 0) continue;
+            const StepLaunch& Lc = step_cfg(b, (int)c);
+            int occ = 1;
+            CK(Lc.occupancy(&occ));
+            occ = std::max(occ, 1);
+            a.tiles = M.d_tiles;
+            a.ntiles = M.n;
+            a.dynamic = 1;
+            CK(Lc.launch(&a, std::min(M.n, b->nsm * occ), b->stream));
+            b->launches++;
+        }
     } else {
         int occ = 1;
         CK(L.occupancy(&occ));
@@ -425,6 +455,96 @@ int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
         b->launches++;
     }
     b->cur = 1 - b->cur;
+    return MHD_OK;
+}
+
+// Tiles (configuration c, longest first) of the patches for which sel(p) holds.
+std::vector<int4> class_tiles(const mhd_bunch* b, int c, const std::vector<char>& sel) {
+    const auto& T = b->tiles[c];
+    std::vector<int4> out;
+    for (int p = 0; p < b->npatch; ++p)
+        if (sel[p]) out.insert(out.end(), T.nat_h.begin() + T.first[p], T.nat_h.begin() + T.first[p] + T.count[p]);
+    std::stable_sort(out.begin(), out.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+    return out;
+}
+
+// MHD_MODE_MIXED autotuning: every patch-size class timed with every configuration (a
+// persistent launch over the class's tiles at dt = 0, two warm-up and four timed), each
+// class assigned its fastest; then the per-configuration tile lists.  The caller saves and
+// restores the state.
+int autotune_mixed(mhd_bunch* b, int* chosen) {
+    const int n = (int)b->cfg_index.size();
+    std::vector<std::array<int, 3>> cls;
+    std::vector<int> cls_of(b->npatch);
+    for (int p = 0; p < b->npatch; ++p) {
+        const std::array<int, 3> s = {b->pn[3 * p], b->pn[3 * p + 1], b->pn[3 * p + 2]};
+        auto it = std::find(cls.begin(), cls.end(), s);
+        cls_of[p] = (int)(it - cls.begin());
+        if (it == cls.end()) cls.push_back(s);
+    }
+    std::vector<int> pick(cls.size(), 0);
+    std::vector<int64_t> cells(cls.size(), 0);
+    for (int p = 0; p < b->npatch; ++p) cells[cls_of[p]] += (int64_t)b->pn[3 * p] * b->pn[3 * p + 1] * b->pn[3 * p + 2];
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int4* d_tmp = nullptr;
+    int rc = MHD_OK;
+    cudaError_t e = cudaSuccess;
+    for (size_t q = 0; q < cls.size() && rc == MHD_OK; ++q) {
+        std::vector<char> sel(b->npatch);
+        for (int p = 0; p < b->npatch; ++p) sel[p] = cls_of[p] == (int)q;
+        float best = 1e30f;
+        for (int c = 0; c < n && rc == MHD_OK; ++c) {
+            const std::vector<int4> tl = class_tiles(b, c, sel);
+            cudaFree(d_tmp);
+            d_tmp = nullptr;
+            e = cudaMalloc(&d_tmp, sizeof(int4) * tl.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(d_tmp, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
+            const StepLaunch& L = step_cfg(b, c);
+            int occ = 1;
+            e = L.occupancy(&occ);
+            if (e != cudaSuccess) break;
+            StepHostArgs a = step_args(b, nullptr, 0.0);
+            a.tiles = d_tmp;
+            a.ntiles = (int)tl.size();
+            a.dynamic = 1;
+            const int grid = std::min((int)tl.size(), b->nsm * std::max(occ, 1));
+            for (int w = 0; w < 6 && e == cudaSuccess; ++w) {
+                if (w == 2) e = cudaEventRecord(e0, b->stream);
+                if (e == cudaSuccess) e = L.launch(&a, grid, b->stream);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (ms < best) {
+                best = ms;
+                pick[q] = c;
+            }
+        }
+        if (e != cudaSuccess) rc = fail(MHD_ECUDA, cudaGetErrorString(e));
+    }
+    cudaFree(d_tmp);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    free_mixed(b);
+    b->mixed.resize(n);
+    for (int c = 0; c < n; ++c) {
+        std::vector<char> sel(b->npatch);
+        bool any = false;
+        for (int p = 0; p < b->npatch; ++p) any |= (sel[p] = pick[cls_of[p]] == c) != 0;
+        if (!any) continue;
+        const std::vector<int4> tl = class_tiles(b, c, sel);
+        CK(cudaMalloc(&b->mixed[c].d_tiles, sizeof(int4) * tl.size()));
+        CK(cudaMemcpy(b->mixed[c].d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice));
+        b->mixed[c].n = (int)tl.size();
+    }
+    if (chosen) *chosen = pick[std::max_element(cells.begin(), cells.end()) - cells.begin()];
     return MHD_OK;
 }
 
@@ -821,7 +941,7 @@ int mhd_bunch_step_device_dt(mhd_bunch* b, const void* dt_dev) {
 
 int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
-    if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_PERSISTENT) return fail(MHD_EINVAL, "bad mode");
+    if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_MIXED) return fail(MHD_EINVAL, "bad mode");
     if (config < -1 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
     release_graph(b);
     b->mode = mode;
@@ -868,7 +988,7 @@ int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
     std::string k = key.str();
     for (auto& ch : k)
         if (ch == ' ') ch = '_';
-    if (cache_path) {
+    if (cache_path && b->mode != MHD_MODE_MIXED) {
         std::ifstream f(cache_path);
         std::string kk;
         int idx;
@@ -896,7 +1016,9 @@ int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
     float best = 1e30f;
     int besti = 0;
     rc = do_fill(b);
-    for (int c = 0; c < n && rc == MHD_OK; ++c) {
+    const bool mixed = b->mode == MHD_MODE_MIXED;
+    if (mixed && rc == MHD_OK) rc = autotune_mixed(b, &besti);
+    for (int c = 0; c < n && rc == MHD_OK && !mixed; ++c) {
         b->config = c;
         // dt = 0 keeps the state unchanged in value; the work is the same as a real step
         for (int w = 0; w < 2 && rc == MHD_OK; ++w) {
@@ -936,9 +1058,9 @@ int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
     }
     if (e != cudaSuccess) return fail(MHD_ECUDA, cudaGetErrorString(e));
     release_graph(b);
-    b->config = besti;
+    if (!mixed) b->config = besti;
     if (chosen) *chosen = besti;
-    if (cache_path) {
+    if (cache_path && !mixed) {
         std::ofstream f(cache_path, std::ios::app);
         f << k << " " << besti << "\n";
     }

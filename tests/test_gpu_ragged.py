@@ -47,6 +47,17 @@ def test_ragged_small_fill_and_modes():
             b.set_mode(mode, cfg)
             b.upload(flat)
             outs.append(interior_global(gpu_steps(b, [2e-3]), geom))
+    # per-class configurations (one persistent launch per configuration in use), before
+    # and after the autotuner assigned them; the autotuner leaves the state as it was
+    b.set_mode(capi.MHD_MODE_MIXED, -1)
+    b.upload(flat)
+    outs.append(interior_global(gpu_steps(b, [2e-3]), geom))
+    b.upload(flat)
+    b.autotune(None)
+    assert np.array_equal(interior_global(b.download(), geom), interior_global(flat, geom))
+    n0 = b.launch_count()
+    outs.append(interior_global(gpu_steps(b, [2e-3]), geom))
+    assert 2 <= b.launch_count() - n0 <= 1 + b.num_configs()   # fill + one launch per configuration in use
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
 
