@@ -465,6 +465,18 @@ def run_ours(args, ws, rank, local):
     b.stream.synchronize()
     mean = lambda i, j: float(np.mean([ev[k][i].elapsed_time(ev[k][j]) for k in range(args.steps)]))
     t_fc, t_step, t_fill, t_cfl = mean(0, 1), mean(1, 2), mean(2, 3), mean(3, 4)
+    # the step with the HLL face flux instead of HLLD (same kernel, runtime switch)
+    b.set_riemann(capi.MHD_RIEMANN_HLL)
+    nh = max(2, min(args.steps, 5))
+    evh = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(nh + 1)]
+    for k in range(nh + 1):            # the first is a warm-up
+        b.fill_cfl_device(dt_dev)
+        evh[k][0].record(b.stream)
+        b.step_device_dt(dt_dev)
+        evh[k][1].record(b.stream)
+    b.stream.synchronize()
+    t_step_hll = float(np.mean([evh[k][0].elapsed_time(evh[k][1]) for k in range(1, nh + 1)]))
+    b.set_riemann(capi.MHD_RIEMANN_HLLD)
     code, msg = b.error()
     if code != 0:
         raise RuntimeError(f"device error during the benchmark: {msg}")
@@ -526,7 +538,8 @@ def run_ours(args, ws, rank, local):
                       "l2": f"inputs larger than L2 (state {b.nbytes / 1e9:.2f} GB per buffer)",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
            "roofline": roof, "hbm_roofline": hbm_roof,
-           "kernels_ms": {"fill_cfl": t_fc, "step": t_step, "fill_guards_alone": t_fill, "cfl_dt_alone": t_cfl},
+           "kernels_ms": {"fill_cfl": t_fc, "step": t_step, "fill_guards_alone": t_fill, "cfl_dt_alone": t_cfl,
+                          "step_hll_flux": t_step_hll},
            "plain_per_patch": {"value": plain, "unit": UNIT, "launches_per_step": geom.npatch + 2,
                                "path": "guard fill + CFL dt + one step launch per patch, eager"},
            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,

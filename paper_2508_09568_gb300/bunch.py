@@ -110,6 +110,11 @@ class MHDBunch:
         assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
         capi.check(self.lib.mhd_bunch_step_device_dt(self.h, ct.c_void_p(dt_dev.data_ptr())))
 
+    def set_riemann(self, riemann: int):
+        """Face-flux solver of later steps: capi.MHD_RIEMANN_HLLD or capi.MHD_RIEMANN_HLL."""
+        capi.check(self.lib.mhd_bunch_set_riemann(self.h, int(riemann)))
+        self._params["riemann"] = int(riemann)
+
     def set_mode(self, mode: int, config: int = -1):
         capi.check(self.lib.mhd_bunch_set_mode(self.h, int(mode), int(config)))
 
