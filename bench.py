@@ -412,7 +412,7 @@ def run_ours(args, ws, rank, local):
         b.close()
         return
     if args.leg == "e2e":
-        rec = e2e_leg(b, host, host_int, geom.interior_cells(), ws, max(2, min(args.steps, 10)))
+        rec = e2e_leg(b, host, host_int, geom.interior_cells(), ws, max(2, min(args.steps, 20)))
         if rank == 0:
             print(json.dumps({"leg": "e2e", **rec}), flush=True)
         b.close()
@@ -506,7 +506,7 @@ def run_ours(args, ws, rank, local):
     async_rec = async_leg(b, host, geom) if rank == 0 and not args.no_extra else None
 
     # ---- end to end through the C ABI on host buffers (H2D + fill + dt + step + D2H per step)
-    e2e = None if args.no_e2e else e2e_leg(b, host, host_int, cells, ws, max(2, min(args.steps, 10)))
+    e2e = None if args.no_e2e else e2e_leg(b, host, host_int, cells, ws, max(2, min(args.steps, 20)))
 
     # ---- roofline of the dominant kernel (the fused step): SIMT-arithmetic bound; the
     # peak is the FMA rate the library's probe kernel measures on this GPU
