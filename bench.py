@@ -158,6 +158,31 @@ def cpu_baseline(steps=1):
                       f"guard fill + step, {el:.2f} s"}
 
 
+def cpu_baseline_configs():
+    """The oracle on host cores on the 1D and 2D configurations: the whole Sod run (256
+    cells, to t = 0.2) and two steps of the 512^2 Orszag-Tang box, in cell-updates/s."""
+    from oracle import mhd as O
+    from paper_2508_09568_gb300 import workloads as W
+    out = {}
+    geom, U, meta = W.sod(ncell=256, npatch=16)
+    ob = O.Bunch(geom, meta["gamma"])
+    P = ob.split(W.to_patches(U, geom))
+    t0 = time.perf_counter()
+    P, t, k = ob.run(P, t_end=0.2)
+    el = time.perf_counter() - t0
+    out["sod_256"] = {"value": 256 * k / el, "unit": UNIT, "steps": k, "s": el}
+    geom, U, meta = W.orszag_tang(ncell=512, patch=32)
+    ob = O.Bunch(geom, meta["gamma"])
+    P = ob.split(W.to_patches(U, geom))
+    dt = float(ob.cfl_dt(ob.fill_guards(P)))
+    t0 = time.perf_counter()
+    for _ in range(2):
+        P = ob.step(P, dt)
+    el = time.perf_counter() - t0
+    out["orszag_tang_512"] = {"value": 512 * 512 * 2 / el, "unit": UNIT, "steps": 2, "s": el}
+    return out
+
+
 def _time_ms(stream, fn, n):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -561,6 +586,7 @@ def run_ours(args, ws, rank, local):
             torch.set_num_threads(nt)
         out["cpu_baseline"]["single_core"] = {"ns_per_cell_update": 1e9 / one["value"], "cores": 1,
                                               "sample": one["sample"]}
+        out["cpu_baseline"]["other_configs"] = cpu_baseline_configs()
     b.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
