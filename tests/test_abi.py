@@ -65,3 +65,23 @@ def test_argument_validation_before_any_device_call(lib):
     r = ct.c_double()
     assert lib.mhd_probe_fma_rate(2, None, ct.byref(r)) == capi.MHD_EINVAL           # real_bytes
     assert lib.mhd_probe_fma_rate(4, None, None) == capi.MHD_EINVAL                   # no output
+    # the largest and smallest patch extents, checked before any allocation
+    assert lib.mhd_bunch_create(4097, 8, 8, 3, 8, 4, 4, ct.byref(h)) == capi.MHD_EINVAL
+    assert b"too large" in lib.mhd_last_error()
+    pn = (ct.c_int32 * 6)(8, 8, 8, 8, 0, 8)
+    assert lib.mhd_bunch_create_ragged(pn, 2, 3, 8, 4, ct.byref(h)) == capi.MHD_EINVAL   # extent 0
+    pn = (ct.c_int32 * 6)(8, 8, 8, 8, 8, 1)
+    assert lib.mhd_bunch_create_ragged(pn, 2, 3, 8, 4, ct.byref(h)) == capi.MHD_EINVAL   # mixed axes
+    # every entry point rejects a NULL handle or output without touching the device
+    n = ct.c_int()
+    i64 = ct.c_int64()
+    sz = ct.c_size_t()
+    assert lib.mhd_bunch_set_mode(None, capi.MHD_MODE_MIXED, -1) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_autotune(None, None, ct.byref(n)) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_interior_size(None, ct.byref(sz), None) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_advance_streamed(None, None, 1, 1, None) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_advance_streamed_interior(None, None, 1, 1, None) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_advance_async(None, 1.0, 1, ct.byref(n), ct.byref(i64)) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_async_round(None, 0, None, None, 0, ct.byref(n)) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_graph_capture(None, 1, None) == capi.MHD_EINVAL
+    assert lib.mhd_bunch_launch_count(None, ct.byref(i64)) == capi.MHD_EINVAL
