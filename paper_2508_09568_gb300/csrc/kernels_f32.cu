@@ -10,6 +10,7 @@ static const StepLaunch kStepF32[] = {
     StepInst<float, 3, 16, 8, 256, 2>::entry(),
     StepInst<float, 3, 8, 8, 128, 3>::entry(),
     StepInst<float, 3, 16, 16, 384>::entry(),
+    StepInst<float, 3, 24, 8, 512, 1, true>::entry(),
     StepInst<float, 2, 16, 16, 256>::entry(),
     StepInst<float, 2, 32, 8, 256>::entry(),
     StepInst<float, 1, 64, 1, 64>::entry(),
