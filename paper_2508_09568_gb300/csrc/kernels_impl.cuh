@@ -88,10 +88,16 @@ static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, int npatch,
 template <typename R>
 static cudaError_t launch_fill_interp(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list,
                                      int nlist, const int* nlist_dev, int grid_y, const int* slice,
-                                     const double* t_old, const double* t_cur, const FillGeom& fg, unsigned* err,
-                                     cudaStream_t s) {
+                                     const double* t_old, const double* t_cur, const FillGeom& fg,
+                                     const int64_t* nboff, int Zp, int64_t pstride, unsigned* err, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
     const int gy = std::min(std::min(nlist, grid_y > 0 ? grid_y : nlist), 65535);
+    if (nboff) {
+        fill_interp_grid_kernel<R><<<dim3(Zp, gy), 128, 0, s>>>(static_cast<R*>(U0), static_cast<R*>(U1), patches,
+                                                                 nboff, list, nlist, nlist_dev, pstride, slice, t_old,
+                                                                 t_cur);
+        return cudaGetLastError();
+    }
     dim3 grid(32, gy);
     fill_interp_kernel<R><<<grid, 256, 0, s>>>(static_cast<R*>(U0), static_cast<R*>(U1), patches, npatch, list, nlist,
                                                nlist_dev, slice, t_old, t_cur, fg, err);

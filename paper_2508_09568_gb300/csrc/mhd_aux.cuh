@@ -513,6 +513,92 @@ __global__ void fill_interp_kernel(R* __restrict__ U0, R* __restrict__ U1, const
     }
 }
 
+// The same for equal patches on a regular grid: sources from the neighbour table (as
+// fill_grid_kernel; the patch owning a source is its state offset over pstride, the state
+// stride of one patch, the patches being stored back to back), one CTA per padded z-plane of
+// a listed patch (blockIdx.x = plane), four ghost cells per thread and pass with both slices
+// of their sources loaded before the stores; the same values as fill_interp_kernel.
+template <typename R>
+__global__ void __launch_bounds__(128) fill_interp_grid_kernel(R* __restrict__ U0, R* __restrict__ U1,
+                                                              const PatchDev* __restrict__ patches,
+                                                              const int64_t* __restrict__ nboff,
+                                                              const int* __restrict__ list, int nlist,
+                                                              const int* nlist_dev, int64_t pstride,
+                                                              const int* __restrict__ slice,
+                                                              const double* __restrict__ t_old,
+                                                              const double* __restrict__ t_cur) {
+    const int nl = nlist_dev ? min(*nlist_dev, nlist) : nlist;
+    const int z = blockIdx.x;
+    for (int L = blockIdx.y; L < nl; L += gridDim.y) {
+        const int p = list[L];
+        const PatchDev pt = patches[p];
+        if (z >= pt.Z) continue;
+        const int64_t* nb = nboff + (int64_t)p * 27;
+        const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy;
+        const int64_t vol = (int64_t)X * Y * pt.Z;
+        const int iz = z - pt.gz;
+        const bool zghost = iz < 0 || iz >= pt.nz;
+        const int nfull = zghost ? X * Y : 2 * gy * X;
+        const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
+        R* plane = (slice[p] ? U1 : U0) + pt.off + (int64_t)z * X * Y;
+        const double tp = t_cur[p];
+        constexpr int NC = 4;
+        for (int k0 = threadIdx.x; k0 < ncnt; k0 += NC * blockDim.x) {
+            int64_t so[NC];
+            int64_t dof[NC];
+            double w[NC];
+            int sq[NC];
+            bool on[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int k = k0 + c * blockDim.x;
+                on[c] = k < ncnt;
+                int x = 0, y = 0;
+                if (on[c]) {
+                    if (k < nfull) {
+                        const int r = k / X;
+                        x = k - r * X;
+                        y = zghost ? r : (r < gy ? r : pt.ny + r);
+                    } else {
+                        const int k2 = k - nfull;
+                        const int r = k2 / (2 * gx), cc = k2 - r * (2 * gx);
+                        y = gy + r;
+                        x = cc < gx ? cc : pt.nx + cc;
+                    }
+                }
+                so[c] = neighbour_source(pt, nb, on[c] ? x - gx : 0, on[c] ? y - gy : 0, on[c] ? iz : 0);
+                const int q = (int)(so[c] / pstride);
+                sq[c] = slice[q];
+                const double den = t_cur[q] - t_old[q];
+                w[c] = den > 0.0 ? (tp - t_old[q]) / den : 1.0;
+                dof[c] = (int64_t)y * X + x;
+            }
+            R vc[NC][8], vo[NC][8];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const R* cur = (sq[c] ? U1 : U0) + so[c];
+                const R* old = (sq[c] ? U0 : U1) + so[c];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    vc[c][v] = on[c] ? cur[v * vol] : R(0);
+                    vo[c][v] = on[c] ? old[v * vol] : R(0);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (!on[c]) continue;
+                const R wr = R(w[c]);
+                R* d = plane + dof[c];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const R o = vo[c][v];
+                    d[v * vol] = w[c] >= 1.0 ? vc[c][v] : (w[c] <= 0.0 ? o : o + wr * (vc[c][v] - o));
+                }
+            }
+        }
+    }
+}
+
 // a2 per listed patch: the maximum CFL rate over the patch's interior cells of its current
 // slice, as the bit pattern of a non-negative double in rate_max[p] (zeroed beforehand;
 // blocks along x share a patch and combine with an integer atomic max, which orders

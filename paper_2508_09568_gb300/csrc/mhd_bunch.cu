@@ -1372,6 +1372,8 @@ int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* ro
     a.dynamic = 1;
     const int step_grid = std::min(T.n, b->nsm * occ);
     const int list_blocks = std::max(1, 2 * b->nsm);
+    // state stride of one patch (equal patches on a regular grid, for the table-driven fill)
+    const int64_t pstride = P > 1 ? b->offs[1] - b->offs[0] : (int64_t)(b->state_bytes / b->rb);
 
     int64_t updates = 0;
     int r = 0, prev = -1;
@@ -1391,7 +1393,7 @@ int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* ro
             CK(cudaGetLastError());
             // guard zones at each patch's own time, then its own CFL dt, clipped
             CK(b->K->fill_interp(b->buf[A], b->buf[1 - A], b->d_patches, P, row, P, nrow, list_blocks, b->d_slice,
-                                 b->d_told, b->d_tcur, b->fg, b->d_err, st));
+                                 b->d_told, b->d_tcur, b->fg, b->d_nboff, b->hp[0].Z, pstride, b->d_err, st));
             CK(b->K->cfl_patch(b->buf[A], b->buf[1 - A], b->d_patches, row, P, nrow, list_blocks, b->d_slice,
                                b->gamma, dxi, act, b->d_rmax, b->d_err, st));
             async_clamp_kernel<<<std::max(1, (P + 255) / 256), 256, 0, st>>>(

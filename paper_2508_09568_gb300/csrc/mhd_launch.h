@@ -55,10 +55,13 @@ struct PrecisionKernels {
     // asynchronous stepping: guard fill of the listed patches at their own times, and
     // their maximum CFL rate (rate_max indexed by patch: the bits of a non-negative double,
     // zeroed beforehand).  The list holds nlist entries, or *nlist_dev (<= nlist) when
-    // nlist_dev is not null; grid_y (> 0) caps the blocks along the list
+    // nlist_dev is not null; grid_y (> 0) caps the blocks along the list.  Regular grids:
+    // nboff the neighbour table, Zp the padded z extent and pstride the state stride of one
+    // patch (table-driven fill), else nboff null (owner map)
     cudaError_t (*fill_interp)(void* U0, void* U1, const PatchDev* patches, int npatch, const int* list, int nlist,
                                const int* nlist_dev, int grid_y, const int* slice, const double* t_old,
-                               const double* t_cur, const FillGeom& fg, unsigned* err, cudaStream_t s);
+                               const double* t_cur, const FillGeom& fg, const int64_t* nboff, int Zp,
+                               int64_t pstride, unsigned* err, cudaStream_t s);
     cudaError_t (*cfl_patch)(const void* U0, const void* U1, const PatchDev* patches, const int* list, int nlist,
                              const int* nlist_dev, int grid_y, const int* slice, double gamma, const double dxi[3],
                              const int act[3], unsigned long long* rate_max, unsigned* err, cudaStream_t s);
