@@ -16,6 +16,7 @@ import ctypes as ct
 import torch
 
 from . import capi
+from .bunch import _check_buffer
 
 
 def _step_into(bunch, U_in: torch.Tensor, U_out: torch.Tensor, dt: float):
@@ -44,6 +45,7 @@ class MHDStep(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, U, bunch, dt):
+        _check_buffer(U, bunch.dtype, bunch.nbytes, True, "U")
         cur = torch.cuda.current_stream(U.device)
         bunch.stream.wait_stream(cur)
         with torch.cuda.stream(bunch.stream):
@@ -73,6 +75,9 @@ class MHDStep(torch.autograd.Function):
 class _Rollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U0, bunch, dt, nsteps, ckpt):
+        _check_buffer(U0, bunch.dtype, bunch.nbytes, True, "U0")
+        if int(nsteps) < 1 or int(ckpt) < 1:
+            raise ValueError("nsteps and ckpt must be at least 1")
         cur_stream = torch.cuda.current_stream(U0.device)
         bunch.stream.wait_stream(cur_stream)
         ckpts = []

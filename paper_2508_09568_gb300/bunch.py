@@ -14,6 +14,28 @@ from . import capi
 from .workloads import Geometry
 
 
+def _check_dt_dev(dt_dev: torch.Tensor, count: int = 1):
+    """dt on the device: `count` float64 elements of a contiguous CUDA tensor."""
+    if not (isinstance(dt_dev, torch.Tensor) and dt_dev.is_cuda and dt_dev.dtype == torch.float64
+            and dt_dev.is_contiguous() and dt_dev.numel() >= count):
+        raise ValueError(f"dt_dev must be a contiguous CUDA float64 tensor of at least {count} element(s)")
+
+
+def _check_buffer(t: torch.Tensor, dtype, nbytes: int, cuda: bool, what: str):
+    """A contiguous tensor of the bunch's dtype holding exactly nbytes, on the device
+    (cuda) or in host memory."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what} must be a torch tensor")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{what} must be in {'device' if cuda else 'host'} memory")
+    if t.dtype != dtype:
+        raise ValueError(f"{what} has dtype {t.dtype}, the bunch computes in {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() * t.element_size() != nbytes:
+        raise ValueError(f"{what} holds {t.numel() * t.element_size()} bytes, the layout needs {nbytes}")
+
+
 class MHDBunch:
     """A bunch of patches on one GPU.
 
@@ -96,18 +118,19 @@ class MHDBunch:
         return dt.value
 
     def cfl_dt_device(self, dt_dev: torch.Tensor):
-        assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
+        _check_dt_dev(dt_dev)
         capi.check(self.lib.mhd_bunch_cfl_dt_device(self.h, ct.c_void_p(dt_dev.data_ptr())))
 
     def fill_cfl_device(self, dt_dev: torch.Tensor):
         """Guard fill then CFL dt into dt_dev (one pass on regular grids)."""
+        _check_dt_dev(dt_dev)
         capi.check(self.lib.mhd_bunch_fill_cfl_device(self.h, ct.c_void_p(dt_dev.data_ptr())))
 
     def step(self, dt: float):
         capi.check(self.lib.mhd_bunch_step(self.h, float(dt)))
 
     def step_device_dt(self, dt_dev: torch.Tensor):
-        assert dt_dev.dtype == torch.float64 and dt_dev.is_cuda
+        _check_dt_dev(dt_dev)
         capi.check(self.lib.mhd_bunch_step_device_dt(self.h, ct.c_void_p(dt_dev.data_ptr())))
 
     def set_riemann(self, riemann: int):
@@ -134,6 +157,8 @@ class MHDBunch:
         return c.value
 
     def graph_capture(self, nsteps: int, dt_dev: torch.Tensor | None = None):
+        if dt_dev is not None:
+            _check_dt_dev(dt_dev, max(int(nsteps), 1))
         ptr = ct.c_void_p(dt_dev.data_ptr()) if dt_dev is not None else None
         capi.check(self.lib.mhd_bunch_graph_capture(self.h, int(nsteps), ptr))
 
@@ -142,8 +167,7 @@ class MHDBunch:
 
     def advance_host(self, host_state: torch.Tensor, nsteps: int) -> float:
         """End to end on host memory (pinned torch tensor in the state layout), in place."""
-        assert host_state.device.type == "cpu" and host_state.dtype == self.dtype
-        assert host_state.numel() * self.rb == self.nbytes
+        _check_buffer(host_state, self.dtype, self.nbytes, False, "host_state")
         t = ct.c_double()
         capi.check(self.lib.mhd_bunch_advance_host(self.h, ct.c_void_p(host_state.data_ptr()), int(nsteps),
                                                    ct.byref(t)))
@@ -153,8 +177,7 @@ class MHDBunch:
         """nsteps steps of a host-resident state (a contiguous CPU tensor of the state layout,
         pinned for overlap) streamed through the GPU every step in nchunks chunks; returns the
         simulated time."""
-        assert host_state.device.type == "cpu" and host_state.is_contiguous()
-        assert host_state.numel() * host_state.element_size() == self.nbytes
+        _check_buffer(host_state, self.dtype, self.nbytes, False, "host_state")
         t = ct.c_double()
         capi.check(self.lib.mhd_bunch_advance_streamed(self.h, ct.c_void_p(host_state.data_ptr()), nsteps, nchunks,
                                                        ct.byref(t)))
@@ -171,9 +194,7 @@ class MHDBunch:
         """As advance_streamed with the host state in the interior layout (owned cells only,
         per patch [8][nz][ny][nx]; workloads.to_interior builds one); returns the simulated
         time."""
-        assert host_interior.device.type == "cpu" and host_interior.is_contiguous()
-        assert host_interior.dtype == self.dtype
-        assert host_interior.numel() * self.rb == self.interior_size()[0]
+        _check_buffer(host_interior, self.dtype, self.interior_size()[0], False, "host_interior")
         t = ct.c_double()
         capi.check(self.lib.mhd_bunch_advance_streamed_interior(self.h, ct.c_void_p(host_interior.data_ptr()), nsteps,
                                                                 nchunks, ct.byref(t)))
@@ -201,8 +222,8 @@ class MHDBunch:
         return out
 
     def step_adjoint(self, dt: float, U_n: torch.Tensor, lam_next: torch.Tensor, lam: torch.Tensor):
-        for t in (U_n, lam_next, lam):
-            assert t.is_cuda and t.dtype == self.dtype and t.numel() * self.rb == self.nbytes
+        for t, what in ((U_n, "U_n"), (lam_next, "lam_next"), (lam, "lam")):
+            _check_buffer(t, self.dtype, self.nbytes, True, what)
         capi.check(self.lib.mhd_bunch_step_adjoint(self.h, float(dt), ct.c_void_p(U_n.data_ptr()),
                                                    ct.c_void_p(lam_next.data_ptr()), ct.c_void_p(lam.data_ptr())))
 
