@@ -21,7 +21,8 @@
  * buffers, the CUDA graph and the error word, all released by mhd_bunch_destroy.
  *
  * Errors: every function returns an mhd_status (0 on success) and never aborts or throws
- * across the ABI.  mhd_last_error() gives a thread-local message for the last failure.
+ * across the ABI (a failed host allocation inside the library returns MHD_ENOMEM).
+ * mhd_last_error() gives a thread-local message for the last failure.
  * Problems found on the device (non-finite or non-positive density / energy after an
  * update, bad patch-table entries, a bounded wait that ran out) are latched in a device
  * error word and reported by the next call that synchronises (mhd_bunch_cfl_dt,

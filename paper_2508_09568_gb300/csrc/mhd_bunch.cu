@@ -13,8 +13,10 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <new>
 #include <numeric>
 #include <sstream>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -33,6 +35,22 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+
+// Catch clauses of every C entry point (a function-try-block): no exception crosses the
+// ABI; host allocation failures become MHD_ENOMEM, anything else MHD_EINVAL with its text.
+#define MHD_CATCH_ALL                                                                         \
+    catch (const std::bad_alloc&) {                                                           \
+        return fail(MHD_ENOMEM, "host memory allocation failed");                             \
+    }                                                                                         \
+    catch (const std::length_error&) {                                                        \
+        return fail(MHD_ENOMEM, "host allocation too large");                                 \
+    }                                                                                         \
+    catch (const std::exception& e_) {                                                        \
+        return fail(MHD_EINVAL, std::string("internal error: ") + e_.what());                 \
+    }                                                                                         \
+    catch (...) {                                                                             \
+        return fail(MHD_EINVAL, "internal error");                                            \
+    }
 
 #define CK(call)                                                                              \
     do {                                                                                      \
@@ -720,7 +738,7 @@ int read_error(mhd_bunch* b, int* code, char* msg, size_t len) {
 
 extern "C" {
 
-int mhd_bunch_create(int nx, int ny, int nz, int guard, int nvar, int npatch, int real_bytes, mhd_bunch** out) {
+int mhd_bunch_create(int nx, int ny, int nz, int guard, int nvar, int npatch, int real_bytes, mhd_bunch** out) try {
     if (npatch <= 0) return fail(MHD_EINVAL, "npatch must be positive");
     std::vector<int32_t> pn(3 * (size_t)npatch);
     for (int p = 0; p < npatch; ++p) {
@@ -729,15 +747,15 @@ int mhd_bunch_create(int nx, int ny, int nz, int guard, int nvar, int npatch, in
         pn[3 * p + 2] = nz;
     }
     return common_create(pn.data(), npatch, guard, nvar, real_bytes, out);
-}
+} MHD_CATCH_ALL
 
 int mhd_bunch_create_ragged(const int32_t* patch_n, int npatch, int guard, int nvar, int real_bytes,
-                            mhd_bunch** out) {
+                            mhd_bunch** out) try {
     return common_create(patch_n, npatch, guard, nvar, real_bytes, out);
-}
+} MHD_CATCH_ALL
 
 int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patch_origin,
-                           const int64_t domain_cells[3], const int32_t bc[6]) {
+                           const int64_t domain_cells[3], const int32_t bc[6]) try {
     if (!b || !dx || !patch_origin || !domain_cells || !bc) return fail(MHD_EINVAL, "NULL argument");
     for (int d = 0; d < 3; ++d) {
         if (!(dx[d] > 0) || !std::isfinite(dx[d])) return fail(MHD_EINVAL, "dx must be positive");
@@ -833,9 +851,9 @@ int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patc
     if (rc != MHD_OK) return rc;
     b->have_geom = true;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_set_params(mhd_bunch* b, double gamma, double courant, int limiter) {
+int mhd_bunch_set_params(mhd_bunch* b, double gamma, double courant, int limiter) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(MHD_EINVAL, "gamma must be > 1");
     if (!(courant > 0.0) || !std::isfinite(courant)) return fail(MHD_EINVAL, "courant must be > 0");
@@ -845,17 +863,17 @@ int mhd_bunch_set_params(mhd_bunch* b, double gamma, double courant, int limiter
     b->courant = courant;
     b->limiter = limiter;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_set_riemann(mhd_bunch* b, int solver) {
+int mhd_bunch_set_riemann(mhd_bunch* b, int solver) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (solver != MHD_RIEMANN_HLLD && solver != MHD_RIEMANN_HLL) return fail(MHD_EINVAL, "bad face-flux solver");
     release_graph(b);
     b->riemann = solver;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_interior_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) {
+int mhd_bunch_interior_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) try {
     if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
     int64_t o = 0;
     for (int p = 0; p < b->npatch; ++p) {
@@ -864,16 +882,16 @@ int mhd_bunch_interior_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_of
     }
     *bytes = (size_t)o * b->rb;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_state_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) {
+int mhd_bunch_state_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) try {
     if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
     *bytes = b->state_bytes;
     if (patch_offsets) std::copy(b->offs.begin(), b->offs.end(), patch_offsets);
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_bind(mhd_bunch* b, void* state, void* state_next, void* cuda_stream) {
+int mhd_bunch_bind(mhd_bunch* b, void* state, void* state_next, void* cuda_stream) try {
     if (!b || !state || !state_next) return fail(MHD_EINVAL, "NULL argument");
     if (state == state_next) return fail(MHD_EINVAL, "state and state_next must differ");
     if ((reinterpret_cast<uintptr_t>(state) & 15) || (reinterpret_cast<uintptr_t>(state_next) & 15))
@@ -884,35 +902,35 @@ int mhd_bunch_bind(mhd_bunch* b, void* state, void* state_next, void* cuda_strea
     b->cur = 0;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_current(const mhd_bunch* b, void** state) {
+int mhd_bunch_current(const mhd_bunch* b, void** state) try {
     if (!b || !state) return fail(MHD_EINVAL, "NULL argument");
     *state = b->buf[b->cur];
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_fill_guards(mhd_bunch* b) {
+int mhd_bunch_fill_guards(mhd_bunch* b) try {
     int rc = ready(b);
     if (rc) return rc;
     return do_fill(b);
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_cfl_dt_device(mhd_bunch* b, void* dt_dev) {
+int mhd_bunch_cfl_dt_device(mhd_bunch* b, void* dt_dev) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
     return do_cfl(b, static_cast<double*>(dt_dev));
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_fill_cfl_device(mhd_bunch* b, void* dt_dev) {
+int mhd_bunch_fill_cfl_device(mhd_bunch* b, void* dt_dev) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
     return do_fill_cfl(b, static_cast<double*>(dt_dev));
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_cfl_dt(mhd_bunch* b, double* dt_host) {
+int mhd_bunch_cfl_dt(mhd_bunch* b, double* dt_host) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!dt_host) return fail(MHD_EINVAL, "dt_host is NULL");
@@ -923,23 +941,23 @@ int mhd_bunch_cfl_dt(mhd_bunch* b, double* dt_host) {
     rc = read_error(b, &code, nullptr, 0);
     if (rc) return rc;
     return code;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_step(mhd_bunch* b, double dt) {
+int mhd_bunch_step(mhd_bunch* b, double dt) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!(dt >= 0) || !std::isfinite(dt)) return fail(MHD_EINVAL, "dt must be finite and >= 0");
     return do_step(b, nullptr, dt);
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_step_device_dt(mhd_bunch* b, const void* dt_dev) {
+int mhd_bunch_step_device_dt(mhd_bunch* b, const void* dt_dev) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!dt_dev) return fail(MHD_EINVAL, "dt_dev is NULL");
     return do_step(b, static_cast<const double*>(dt_dev), 0.0);
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) {
+int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_MIXED) return fail(MHD_EINVAL, "bad mode");
     if (config < -1 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
@@ -947,15 +965,15 @@ int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) {
     b->mode = mode;
     b->config = config;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_num_configs(const mhd_bunch* b, int* nconfig) {
+int mhd_bunch_num_configs(const mhd_bunch* b, int* nconfig) try {
     if (!b || !nconfig) return fail(MHD_EINVAL, "NULL argument");
     *nconfig = (int)b->cfg_index.size();
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_config_info(const mhd_bunch* b, int config, int* tile_x, int* tile_y, int* threads) {
+int mhd_bunch_config_info(const mhd_bunch* b, int config, int* tile_x, int* tile_y, int* threads) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (config < 0 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
     const StepLaunch& L = step_cfg(b, config);
@@ -963,9 +981,9 @@ int mhd_bunch_config_info(const mhd_bunch* b, int config, int* tile_x, int* tile
     if (tile_y) *tile_y = L.ty;
     if (threads) *threads = L.nt;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
+int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) try {
     int rc = ready(b);
     if (rc) return rc;
     const int n = (int)b->cfg_index.size();
@@ -1065,9 +1083,9 @@ int mhd_bunch_autotune(mhd_bunch* b, const char* cache_path, int* chosen) {
         f << k << " " << besti << "\n";
     }
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_graph_capture(mhd_bunch* b, int nsteps, void* dt_dev) {
+int mhd_bunch_graph_capture(mhd_bunch* b, int nsteps, void* dt_dev) try {
     int rc = ready(b);
     if (rc) return rc;
     if (nsteps <= 0) return fail(MHD_EINVAL, "nsteps must be positive");
@@ -1108,9 +1126,9 @@ int mhd_bunch_graph_capture(mhd_bunch* b, int nsteps, void* dt_dev) {
     b->graph_steps = nsteps;
     b->graph_start = cur0;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_graph_launch(mhd_bunch* b) {
+int mhd_bunch_graph_launch(mhd_bunch* b) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!b->gexec[0]) return fail(MHD_ESTATE, "no captured graph");
@@ -1122,9 +1140,9 @@ int mhd_bunch_graph_launch(mhd_bunch* b) {
     b->launches += (int64_t)nn;
     if (b->graph_steps & 1) b->cur = 1 - b->cur;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t_out) {
+int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t_out) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!host_state || nsteps < 0) return fail(MHD_EINVAL, "bad argument");
@@ -1148,9 +1166,9 @@ int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t
     if (rc) return rc;
     if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
     return code;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int nchunks, double* t_out) {
+int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int nchunks, double* t_out) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!host_state || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1215,10 +1233,10 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
     if (rc) return rc;
     if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
     return code;
-}
+} MHD_CATCH_ALL
 
 int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int nsteps, int nchunks,
-                                        double* t_out) {
+                                        double* t_out) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!host_interior || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1312,9 +1330,9 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
     if (rc) return rc;
     if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
     return code;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* rounds, int64_t* patch_updates) {
+int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* rounds, int64_t* patch_updates) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!(t_span >= 0) || !std::isfinite(t_span) || max_rounds < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1445,9 +1463,9 @@ int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* ro
     for (int p = 0; p < P; ++p)
         if (t_cur[p] < t_span) return fail(MHD_ESTATE, "max_rounds reached before every patch arrived at t_span");
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_async_round(const mhd_bunch* b, int round, int32_t* patches, double* dts, int cap, int* n) {
+int mhd_bunch_async_round(const mhd_bunch* b, int round, int32_t* patches, double* dts, int cap, int* n) try {
     if (!b || !n) return fail(MHD_EINVAL, "NULL argument");
     if (round < 0 || round >= (int)b->log_patches.size()) return fail(MHD_EINVAL, "no such round");
     const auto& lp = b->log_patches[round];
@@ -1460,18 +1478,18 @@ int mhd_bunch_async_round(const mhd_bunch* b, int round, int32_t* patches, doubl
         }
     }
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_get_error(mhd_bunch* b, int* code, char* msg, size_t len) {
+int mhd_bunch_get_error(mhd_bunch* b, int* code, char* msg, size_t len) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     return read_error(b, code, msg, len);
-}
+} MHD_CATCH_ALL
 
-int mhd_bunch_launch_count(const mhd_bunch* b, int64_t* count) {
+int mhd_bunch_launch_count(const mhd_bunch* b, int64_t* count) try {
     if (!b || !count) return fail(MHD_EINVAL, "NULL argument");
     *count = b->launches;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
 
 void mhd_bunch_destroy(mhd_bunch* b) {
     if (!b) return;
@@ -1520,7 +1538,7 @@ const char* mhd_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
 
-extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, const void* lam_next, void* lam) {
+extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, const void* lam_next, void* lam) try {
     int rc = ready(b);
     if (rc) return rc;
     if (!U_n || !lam_next || !lam) return fail(MHD_EINVAL, "NULL argument");
@@ -1568,4 +1586,4 @@ extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, 
     CK(b->K->adjoint(a, b->fg, b->d_err, b->stream, &n));
     b->launches += n;
     return MHD_OK;
-}
+} MHD_CATCH_ALL
