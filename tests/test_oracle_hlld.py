@@ -3,8 +3,9 @@
 Every reference value here is written independently of the oracle: the physical flux of
 Eq. 6 is retyped from the equation, HLLC (the B = 0 limit) from its textbook definition,
 the exactness of HLLD on isolated contacts and rotational discontinuities follows from
-its construction (Miyoshi & Kusano 2005), and the 1D HLL induction flux from the HLL
-formula applied to the induction equation.
+its construction (Miyoshi & Kusano 2005), the invariance of a face Riemann problem under
+rotation of the transverse plane is a symmetry of the equations, and the 1D HLL induction
+flux from the HLL formula applied to the induction equation.
 """
 import math
 
@@ -68,6 +69,35 @@ def test_mirror_symmetry():
     sign = [-1, 1, -1, -1, -1]
     for a, b, s in zip(F, Fm, sign):
         assert np.allclose(s * a, b, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("solver", ["hlld", "hll"])
+def test_rotation_about_the_face_normal(solver):
+    """Turning the transverse plane by an angle (velocity and field together) is a symmetry
+    of the face Riemann problem: the mass, normal-momentum and energy fluxes are unchanged
+    and the transverse momentum flux turns with the plane."""
+    rng = np.random.default_rng(14)
+    n = 600
+    L, R = rand_state(rng, n), rand_state(rng, n)
+    bn = rng.normal(0, 1, n)
+    th = rng.uniform(0, 2 * np.pi, n)
+    c, s_ = np.cos(th), np.sin(th)
+
+    def turn(S):
+        rho, un, ut1, ut2, P, bt1, bt2 = S
+        return [rho, un, c * ut1 - s_ * ut2, s_ * ut1 + c * ut2, P, c * bt1 - s_ * bt2, s_ * bt1 + c * bt2]
+
+    def flux(A, B):
+        if solver == "hlld":
+            return call_hlld(A, B, bn)
+        return [f.numpy() for f in mhd.hll([T(a) for a in A], [T(a) for a in B], T(bn), G)]
+
+    F, Fr = flux(L, R), flux(turn(L), turn(R))
+    scale = max(np.abs(f).max() for f in F)
+    for k in (0, 1, 4):
+        assert np.max(np.abs(Fr[k] - F[k])) <= 1e-12 * scale, k
+    assert np.max(np.abs(Fr[2] - (c * F[2] - s_ * F[3]))) <= 1e-12 * scale
+    assert np.max(np.abs(Fr[3] - (s_ * F[2] + c * F[3]))) <= 1e-12 * scale
 
 
 def test_flux_is_continuous_in_states():

@@ -6,11 +6,13 @@ What fixes the expected values:
   * the discrete face divergence kept at its initial value (constrained transport, Eq. 12);
   * the point symmetry of the Orszag-Tang vortex (Sec. 3.1);
   * second-order convergence on smooth linear waves, whose exact solution is the
-    translated initial profile;
+    translated initial profile, and second-order self-convergence on a large-amplitude
+    nonlinear simple wave (which the linear waves cannot see in the nonlinear terms);
   * free-stream preservation, exact slopes on linear data, exact edge averages of
     Eqs. 8-11 on bilinear data;
   * independence of the result from how the box is cut into patches (the guard fill);
-  * closed-form CFL steps of uniform states.
+  * closed-form CFL steps of uniform states, and a dt that depends only on interior
+    cells (and their far faces), whatever the ghost values and the patch cut.
 """
 import math
 
@@ -139,6 +141,35 @@ def wave2d(N, limiter, A=1e-6):
     return np.abs(Gs[5] - U[5]).mean() / A
 
 
+@pytest.mark.parametrize("limiter,order", [(0, 1.7), (1, 1.95)])
+def test_self_convergence_of_a_nonlinear_simple_wave(limiter, order):
+    """A large-amplitude isentropic simple wave (rho = 1 + 0.4 sin 2 pi x, p = rho^gamma /
+    gamma, u = 2 (c - 1) / (gamma - 1)) steepens without a shock until t ~ 0.2.  At
+    t = 0.15 the differences between runs at N and 2N cells (the finer one averaged onto
+    the coarser cells) fall by about 4 per refinement for a second-order scheme; unlike the
+    linear waves above, this exercises the nonlinear terms of the predictor and the fluxes.
+    """
+    def run1d(N):
+        geom = W.uniform_geometry([N, 1, 1], [N // 4, 1, 1], dx=[1.0 / N, 1.0, 1.0])
+        x = (np.arange(N) + 0.5) / N
+        rho = 1.0 + 0.4 * np.sin(2 * np.pi * x)
+        c = rho ** ((G53 - 1) / 2)
+        f = lambda q: np.reshape(q, (1, 1, N))
+        z = np.zeros((1, 1, N))
+        U = W.conserved_from_setup(f(rho), (f(2.0 / (G53 - 1) * (c - 1.0)), z, z), f(rho ** G53 / G53),
+                                   (z, z, z), G53)
+        return run(geom, U, G53, limiter=limiter, t_end=0.15)[0][:, 0, 0, :]
+
+    sols = {N: run1d(N) for N in (32, 64, 128, 256)}
+    diffs = []
+    for N in (32, 64, 128):
+        fine = sols[2 * N]
+        diffs.append(np.abs(0.5 * (fine[:, 0::2] + fine[:, 1::2]) - sols[N]).mean(axis=1))
+    for v in (0, 1, 4):                                   # rho, rho u, E
+        for k in range(2):
+            assert np.log2(diffs[k][v] / diffs[k + 1][v]) >= order, (v, k, diffs)
+
+
 def test_convergence_order_2d_oblique_alfven():
     e = [wave2d(N, 1) for N in (16, 32, 64)]
     rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
@@ -251,6 +282,37 @@ def test_cfl_dt_closed_form():
     cyz = math.sqrt(cs2 + ca2)                # field across y and z
     rate = (0.3 + cx) / 0.1 + (0.4 + cyz) / 0.2 + (0.1 + cyz) / 0.25
     assert math.isclose(B.cfl_dt(P_), 0.8 / rate, rel_tol=1e-14)
+
+
+def test_cfl_dt_reads_only_interior_cells_and_their_high_faces():
+    """a2 takes its maximum over interior cells: every ghost value may change except the
+    face fields of the first high ghost layer (the far faces of the last interior cells)
+    without changing dt, and dt is the same bitwise however the box is cut into patches."""
+    geom, U, meta = W.small_box(ncell=(16, 16, 16), patch=(8, 8, 8), seed=19, amp=0.6)
+    gamma = meta["gamma"]
+    B = mhd.Bunch(geom, gamma)
+    P = B.fill_guards(B.split(W.to_patches(U, geom)))
+    dt = float(B.cfl_dt(P))
+    g, n = 3, 8
+    Q = []
+    for X in P:
+        Y = X.clone()
+        keep = Y.clone()
+        Y[:, :g] = 1e3
+        Y[:, g + n:] = 1e3
+        Y[:, :, :g] = 1e3
+        Y[:, :, g + n:] = 1e3
+        Y[:, :, :, :g] = 1e3
+        Y[:, :, :, g + n:] = 1e3
+        Y[5, g:g + n, g:g + n, g + n] = keep[5, g:g + n, g:g + n, g + n]   # far x-faces
+        Y[6, g:g + n, g + n, g:g + n] = keep[6, g:g + n, g + n, g:g + n]   # far y-faces
+        Y[7, g + n, g:g + n, g:g + n] = keep[7, g + n, g:g + n, g:g + n]   # far z-faces
+        Q.append(Y)
+    assert float(B.cfl_dt(Q)) == dt
+    for patch in ((16, 16, 16), (4, 8, 16), (16, 4, 8)):
+        g2 = W.uniform_geometry([16] * 3, list(patch), dx=geom.dx)
+        B2 = mhd.Bunch(g2, gamma)
+        assert float(B2.cfl_dt(B2.fill_guards(B2.split(W.to_patches(U, g2))))) == dt, patch
 
 
 def test_cfl_dt_ignores_collapsed_axes():
