@@ -75,6 +75,34 @@ def test_fill_interpolates_linearly_in_time():
         assert torch.allclose(got, want, rtol=1e-14, atol=1e-14), p
 
 
+def test_fill_is_exact_for_fields_linear_in_time():
+    """Every patch holds two slices of one field linear in time, f(t) = A + t B, at slice
+    times of its own (all different); a patch's guard fill at its own time t_p, inside every
+    neighbour's slice interval, is the window of f(t_p): linear interpolation between a
+    neighbour's two slices reproduces a linear function of time at any t_p."""
+    geom, A, meta = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=7)
+    _, Bf, _ = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=8)
+    ob = O.Bunch(geom, meta["gamma"])
+    PA, PB = ob.split(W.to_patches(A, geom)), ob.split(W.to_patches(Bf, geom))
+    rng = np.random.default_rng(21)
+    P = geom.npatch
+    t_old = list(rng.uniform(0.0, 0.3, P))
+    t_cur = list(rng.uniform(0.7, 1.0, P))
+    old = [PA[q] + t_old[q] * PB[q] for q in range(P)]
+    cur = [PA[q] + t_cur[q] * PB[q] for q in range(P)]
+    GA = torch.tensor(A)
+    GB = torch.tensor(Bf)
+    for p in range(P):
+        t_p = float(rng.uniform(0.35, 0.65))      # inside every neighbour's interval
+        t = list(t_cur)
+        t[p] = t_p
+        cur_p = list(cur)
+        cur_p[p] = PA[p] + t_p * PB[p]
+        got = O.fill_guards_at(cur_p, old, t, t_old, geom, p)
+        want = O.window(GA + t_p * GB, geom.origin[p], geom.patch_n[p], geom.gvec, geom.domain, geom.bc)
+        assert torch.allclose(got, want, rtol=0, atol=1e-13), p
+
+
 def test_readiness_rule_closed_forms():
     geom, U, meta = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=5)
     ab = O.AsyncBunch(geom, meta["gamma"])
