@@ -100,6 +100,26 @@ def test_rotation_about_the_face_normal(solver):
     assert np.max(np.abs(Fr[3] - (s_ * F[2] + c * F[3]))) <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("alpha", [1e-14, 1e12])
+def test_scaling_of_density_pressure_and_field(alpha):
+    """Ideal MHD is invariant under rho -> a rho, P -> a P, B -> sqrt(a) B with the
+    velocities unchanged (all signal speeds stay the same); every face flux then scales by
+    a.  This includes the solver's degenerate-state test, which compares D with Bn^2."""
+    rng = np.random.default_rng(15)
+    n = 800
+    L, R = rand_state(rng, n), rand_state(rng, n)
+    bn = rng.normal(0, 1, n)
+    bn[:100] = 1e-9 * bn[:100]                # nearly degenerate (Bn -> 0) faces too
+    def scale(S):
+        rho, un, ut1, ut2, P, bt1, bt2 = S
+        r = math.sqrt(alpha)
+        return [alpha * rho, un, ut1, ut2, alpha * P, r * bt1, r * bt2]
+    F = call_hlld(L, R, bn)
+    Fs = call_hlld(scale(L), scale(R), math.sqrt(alpha) * bn)
+    for k in range(5):
+        assert np.allclose(Fs[k], alpha * F[k], rtol=1e-9, atol=1e-12 * alpha * np.abs(F[k]).max()), k
+
+
 def test_flux_is_continuous_in_states():
     rng = np.random.default_rng(3)
     L, R = rand_state(rng, 200), rand_state(rng, 200)
