@@ -8,6 +8,15 @@ from oracle import mhd as O
 from paper_2508_09568_gb300 import workloads as W
 
 TOL_STEP = {torch.float64: 1e-12, torch.float32: 1e-5}
+# element-wise bound per step: max |a - b| over the interior cells of a variable, divided
+# by the largest magnitude of that quantity (max_rel).  FP32: one cell's value comes from
+# flux differences of O(1) terms (|F| ~ the largest total pressure or energy flux) with
+# dt/dx <= 0.8 and a few hundred rounded operations each, so its error is a few 1e-6 of
+# the scale; 1e-4 leaves a margin of about 10 and still fails a single cell that is off by
+# 0.01 % of the scale, far below what a wrong face, edge or ragged-tail cell would give.
+# FP64: the same argument with 2^-53 gives ~1e-13; 1e-10 is the same margin as the L1
+# bound of multi-step runs.
+TOL_MAX = {torch.float64: 1e-10, torch.float32: 1e-4}
 
 
 def interior_global(flat, geom):
@@ -22,6 +31,41 @@ def rel_l1(a, b, floor=1e-300):
         num = np.abs(a[v] - b[v]).sum()
         out.append(num / den if den > floor else num)
     return np.array(out)
+
+
+# scale groups of max_rel: momentum and face field are taken as vectors, so that a
+# component that is zero everywhere (the 1D and 2D boxes, the uniform-field boxes) is
+# measured against the magnitude of its vector
+_GROUPS = ((0,), (1, 2, 3), (1, 2, 3), (1, 2, 3), (4,), (5, 6, 7), (5, 6, 7), (5, 6, 7))
+
+
+def max_rel(a, b):
+    """Per-variable max |a - b| over interior cells divided by the largest magnitude of the
+    variable (of the momentum or face-field vector for their components)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    out = []
+    for v in range(8):
+        g = _GROUPS[v]
+        if len(g) == 1:
+            scale = np.abs(b[v]).max()
+        else:
+            scale = np.sqrt(sum(b[c] ** 2 for c in g)).max()
+        num = np.abs(a[v] - b[v]).max()
+        out.append(num / scale if scale > 0 else num)
+    return np.array(out)
+
+
+def assert_parity(got, ref, dtype, l1=None, mx=None, what=""):
+    """Relative L1 per variable (the tolerance of the scheme's parity) and the element-wise
+    bound, on interior arrays (8, ...)."""
+    l1 = TOL_STEP[dtype] if l1 is None else l1
+    mx = TOL_MAX[dtype] if mx is None else mx
+    e1 = rel_l1(got, ref)
+    em = max_rel(got, ref)
+    assert np.all(e1 <= l1), (what, "rel L1", e1)
+    assert np.all(em <= mx), (what, "max", em)
+    return e1, em
 
 
 def rounded(flat, dtype):

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import interior_global, rel_l1, rounded
+from helpers import assert_parity, interior_global, rounded
 from oracle import mhd as O
 from paper_2508_09568_gb300 import workloads as W
 
@@ -33,9 +33,9 @@ def _run(geom, U, gamma, dtype, spans=3.0):
     return b, flat, t_span, rounds, updates, log, final, ready_sets, local_dts, t_cur
 
 
-@pytest.mark.parametrize("dtype,tol_dt,tol", [(torch.float64, 1e-12, 1e-11), (torch.float32, 2e-6, 5e-5)],
-                         ids=["f64", "f32"])
-def test_async_schedule_and_states_match_oracle(dtype, tol_dt, tol):
+@pytest.mark.parametrize("dtype,tol_dt,tol,tol_max", [(torch.float64, 1e-12, 1e-11, 1e-10),
+                                                     (torch.float32, 2e-6, 5e-5, 5e-4)], ids=["f64", "f32"])
+def test_async_schedule_and_states_match_oracle(dtype, tol_dt, tol, tol_max):
     # velocity amplitude large enough that the patches' own time steps differ
     geom, U, meta = W.small_box(ncell=(24, 16, 16), patch=(8, 8, 8), seed=33, amp=0.9)
     b, flat, t_span, rounds, updates, log, final, ready_sets, local_dts, t_cur = _run(geom, U, meta["gamma"], dtype)
@@ -49,8 +49,7 @@ def test_async_schedule_and_states_match_oracle(dtype, tol_dt, tol):
     ob = O.Bunch(geom, meta["gamma"])
     ref = interior_global(ob.join(final), geom)
     got = interior_global(b.download(), geom)
-    err = rel_l1(got, ref)
-    assert np.all(err <= tol), err
+    assert_parity(got, ref, dtype, l1=tol, mx=tol_max)
 
 
 def test_async_ragged_bunch_fp64():
@@ -62,8 +61,8 @@ def test_async_ragged_bunch_fp64():
         assert list(plist) == rs
         assert np.allclose(dts, ldt, rtol=1e-12, atol=0)
     ob = O.Bunch(geom, meta["gamma"])
-    err = rel_l1(interior_global(b.download(), geom), interior_global(ob.join(final), geom))
-    assert np.all(err <= 1e-11), err
+    assert_parity(interior_global(b.download(), geom), interior_global(ob.join(final), geom), torch.float64,
+                  l1=1e-11, mx=1e-10)
 
 
 def test_async_many_rounds_and_max_rounds_cut():
@@ -82,8 +81,8 @@ def test_async_many_rounds_and_max_rounds_cut():
         assert list(plist) == rs
         assert np.allclose(dts, ldt, rtol=1e-12, atol=0)
     ob = O.Bunch(geom, meta["gamma"])
-    err = rel_l1(interior_global(b.download(), geom), interior_global(ob.join(final), geom))
-    assert np.all(err <= 1e-11), err
+    assert_parity(interior_global(b.download(), geom), interior_global(ob.join(final), geom), torch.float64,
+                  l1=1e-11, mx=1e-10)
     cut = rounds - 5
     b2 = MHDBunch(geom, dtype=torch.float64, gamma=meta["gamma"])
     b2.upload(flat)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import TOL_STEP, gpu_bunch, gpu_steps, interior_global, oracle_steps, rel_l1, rounded
+from helpers import assert_parity, gpu_bunch, gpu_steps, interior_global, oracle_steps, rounded
 from paper_2508_09568_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +31,7 @@ def test_single_periodic_patch(dtype):
     b.step(dt)
     got = interior_global(b.download(), geom)
     ref = interior_global(oracle_steps(geom, flat, meta["gamma"], [dt], dtype=dtype), geom)
-    assert np.all(rel_l1(got, ref) <= TOL_STEP[dtype])
+    assert_parity(got, ref, dtype)
 
 
 @pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])

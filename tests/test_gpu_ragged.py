@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import TOL_STEP, gpu_bunch, gpu_steps, interior_global, oracle_bunch, oracle_steps, rel_l1, rounded
+from helpers import assert_parity, gpu_bunch, gpu_steps, interior_global, oracle_bunch, oracle_steps, rounded
 from oracle import mhd as O
 from paper_2508_09568_gb300 import capi
 from paper_2508_09568_gb300 import workloads as W
@@ -29,8 +29,7 @@ def test_ragged_small_per_step_parity(dtype):
         ref = oracle_steps(geom, flat, meta["gamma"], [dt], dtype=dtype)
         b.upload(flat)
         got = gpu_steps(b, [dt])
-        err = rel_l1(interior_global(got, geom), interior_global(ref, geom))
-        assert np.all(err <= TOL_STEP[dtype]), err
+        assert_parity(interior_global(got, geom), interior_global(ref, geom), dtype)
         flat = rounded(got, dtype)
 
 
@@ -87,8 +86,7 @@ def test_ragged_box_full_size_sampled_and_invariants():
             Z, Y, X = geom.padded(p)
             gp = got[offs[p]: offs[p] + 8 * X * Y * Z].reshape(8, Z, Y, X).astype(np.float64)
             sl = (slice(None),) + tuple(slice(3, 3 + size) for _ in range(3))
-            err = rel_l1(gp[sl], out[sl])
-            assert np.all(err <= TOL_STEP[torch.float32]), (size, p, err)
+            assert_parity(gp[sl], out[sl], torch.float32, what=(size, int(p)))
     # 50 steps of the whole box: conservation and div B
     G0 = W.from_patches(flat, geom)
     b.upload(flat)

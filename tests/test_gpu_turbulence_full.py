@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import TOL_STEP, rel_l1
+from helpers import TOL_MAX, TOL_STEP, max_rel, rel_l1
 from oracle import mhd as O
 from paper_2508_09568_gb300 import capi
 from paper_2508_09568_gb300 import workloads as W
@@ -118,6 +118,9 @@ def test_turbulence_box_full_size_sampled_and_invariants(dtype):
         err = rel_l1(a, r)[:5]
         errb = np.abs(a[5:8] - r[5:8]).sum() / np.abs(r[5:8]).sum()
         assert np.all(err <= TOL_STEP[dtype]) and errb <= TOL_STEP[dtype], (int(p), err, errb)
+        # element by element (momentum and field measured against their vectors' scale)
+        em = max_rel(a, r)
+        assert np.all(em <= TOL_MAX[dtype]), (int(p), em)
     if dtype == torch.float64:
         code, msg = b.error()
         assert code == 0, msg
