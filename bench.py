@@ -241,7 +241,7 @@ def ragged_leg(dev, steps):
     """The ragged box: 1566 patches of 16^3 / 24^3 / 32^3 (24.55 M cells), FP32, the step in a
     CUDA graph with one persistent launch per tile configuration, configurations chosen per
     patch-size class by the autotuner; beside it one configuration for the whole bunch and
-    the one-launch-per-patch path."""
+    the one-launch-per-patch path and the workload's own bunches (one launch per bunch)."""
     from paper_2508_09568_gb300 import capi
     from paper_2508_09568_gb300 import workloads as W
     from paper_2508_09568_gb300.bunch import MHDBunch
@@ -265,6 +265,10 @@ def ragged_leg(dev, steps):
     b.autotune(None)
     ms = graph_ms()
     cells = geom.interior_cells()
+    # the workload's own bunches (sizes U{8..512}): one persistent launch per bunch
+    b.set_bunches(geom.bunches)
+    b.set_mode(capi.MHD_MODE_BUNCH_LISTS, cfg)
+    ms_lists = graph_ms()
     b.set_mode(capi.MHD_MODE_PER_PATCH, cfg)
     dt_dev = torch.zeros(1, dtype=torch.float64, device=dev)
 
@@ -284,6 +288,9 @@ def ragged_leg(dev, steps):
             "mode": "one persistent launch per tile configuration, configurations chosen per patch-size class",
             "single_configuration": {"value": cells / (ms_single * 1e-3), "ms_per_step": ms_single,
                                      "config_index": cfg},
+            "bunch_lists": {"value": cells / (ms_lists * 1e-3), "ms_per_step": ms_lists, "config_index": cfg,
+                            "bunches": len(geom.bunches), "launches_per_step": len(geom.bunches) + 1,
+                            "mode": "one persistent launch per bunch of the workload (sizes drawn from 8..512)"},
             "plain_per_patch": {"value": cells / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                                 "launches_per_step": geom.npatch + 2}}
 

@@ -69,9 +69,19 @@ enum { MHD_RIEMANN_HLLD = 0, MHD_RIEMANN_HLL = 1 };
  *                tile configuration (chosen per class by mhd_bunch_autotune) and the
  *                update is one persistent launch per configuration in use, over the
  *                tiles of its patches; until mhd_bunch_autotune has run in this mode, as
- *                PERSISTENT.  The streamed and asynchronous advances use the single
- *                configuration of mhd_bunch_set_mode in every mode.                     */
-enum { MHD_MODE_PER_PATCH = 0, MHD_MODE_BUNCHED = 1, MHD_MODE_PERSISTENT = 2, MHD_MODE_MIXED = 3 };
+ *                PERSISTENT.
+ *   BUNCH_LISTS: the paper's bunches (Secs. 2.3-2.4: a bunch of patches per kernel
+ *                invocation): one persistent launch per bunch of mhd_bunch_set_bunches,
+ *                in list order, over that bunch's tiles; MHD_ESTATE until bunches are set.
+ * The streamed and asynchronous advances use the single configuration of
+ * mhd_bunch_set_mode in every mode.                                                      */
+enum {
+    MHD_MODE_PER_PATCH = 0,
+    MHD_MODE_BUNCHED = 1,
+    MHD_MODE_PERSISTENT = 2,
+    MHD_MODE_MIXED = 3,
+    MHD_MODE_BUNCH_LISTS = 4
+};
 
 /* Create a bunch of npatch equal patches of nx*ny*nz active cells.
  * guard: ghost width on active axes; must be >= 3 (the update reads two ghost cells
@@ -173,6 +183,14 @@ int mhd_bunch_advance_async(mhd_bunch *b, double t_span, int max_rounds, int *ro
 int mhd_bunch_async_round(const mhd_bunch *b, int round, int32_t *patches, double *dts, int cap,
                           int *n);
 
+/* Bunches of the patches for MHD_MODE_BUNCH_LISTS (Secs. 2.3-2.4: the solver updates a
+ * bunch of patches per call; the paper's best bunches hold 100-400 patches).  Bunch q holds
+ * patches[starts[q] .. starts[q+1]-1]; starts has nbunch+1 entries, starts[0] = 0 and
+ * starts[nbunch] = npatch, and patches lists every patch exactly once (MHD_EINVAL
+ * otherwise, nothing changed).  Copied by the library (its tile lists are built here, on
+ * the device); a later set_geometry discards them.  After set_geometry (MHD_ESTATE before). */
+int mhd_bunch_set_bunches(mhd_bunch *b, const int32_t *patches, const int32_t *starts, int nbunch);
+
 /* Launch mode of the update (MHD_MODE_*) and tile configuration index (0..n-1 from
  * mhd_bunch_num_configs; -1 = library default).  Every mode and every configuration
  * computes bitwise the same state. */
@@ -242,6 +260,31 @@ int mhd_bunch_interior_size(const mhd_bunch *b, size_t *bytes, int64_t *patch_of
 int mhd_bunch_advance_streamed_interior(mhd_bunch *b, void *host_interior, int nsteps, int nchunks,
                                         double *t_out);
 
+/* Host-resident state larger than the device memory this call may use (the paper's
+ * bunches staged from the host every update, Secs. 2.4 and 4, for a domain that does not
+ * fit in HBM).  host_state holds the state in the interior layout (mhd_bunch_interior_size
+ * bytes; page-locked for the copies to overlap); host_scratch is a second buffer of the
+ * same size (different from host_state) that the call writes freely.  After nsteps steps
+ * host_state holds the new state and *t_out (may be NULL) the simulated time.
+ *
+ * Only for a 3D box of equal patches on a grid, listed x fastest, then y, then z (as
+ * mhd_bunch_create makes them); its z-layers of patches are the unit of transfer.  The
+ * call allocates at most device_budget bytes of device memory for its working set (the
+ * handle's own tables, allocated earlier, come on top; bind is not needed): a ring of
+ * L+2 padded layers for U^n and one for U^{n+1}, upload and download stages and tables,
+ * with L the largest chunk of layers that fits (MHD_ENOMEM if one layer does not).  Per
+ * step, two passes over the chunks, each window of layers uploaded once per pass, its
+ * layers above and below included: (1) guard fill + CFL rates of every chunk, dt = the
+ * smallest chunk dt, i.e. the global CFL dt; (2) guard fill and update of each chunk,
+ * its new interior copied back into the other host buffer.  The results equal those of
+ * the device-resident steps (mhd_bunch_fill_cfl_device + mhd_bunch_step_device_dt)
+ * bitwise.  Runs on cuda_stream (NULL: legacy default stream) and the library's copy
+ * streams and synchronises them; returns the device error word as mhd_bunch_get_error
+ * would.  MHD_EINVAL for other geometries or bad arguments, MHD_ESTATE before
+ * set_geometry. */
+int mhd_bunch_advance_out_of_core(mhd_bunch *b, void *host_state, void *host_scratch, int nsteps,
+                                  size_t device_budget, void *cuda_stream, double *t_out);
+
 /* Adjoint of one step at fixed dt (the reverse of mhd_bunch_step, including the guard
  * fill): given U^n (interior valid; ghosts are re-filled internally) and the cotangent
  * lam_next of U^{n+1} (interior cells and owned faces), writes
@@ -268,13 +311,13 @@ const char *mhd_last_error(void);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free CFL time step.  The paper has no counterpart: this entry point exists
- * for callers that must not allocate device memory through the CUDA runtime -- code
- * running while its stream is captured into a CUDA graph, hosts whose framework hands
- * out all device memory from its own pool, real-time loops that cannot afford an
- * allocation.  It needs no handle and calls no cudaMalloc / cudaFree (nor any other
- * allocating routine): its scratch is a static device array inside the library holding
- * one partial maximum per patch, MHD_NOALLOC_MAX_PATCHES entries (128 KB of doubles plus
- * a 4-byte counter), which every GPU that loads the library keeps until the process exits.
+ * for callers that must not allocate device memory through the CUDA runtime -- hosts whose
+ * framework hands out all device memory from its own pool and accounts for every byte,
+ * real-time loops that cannot afford an allocation.  It needs no handle and calls no
+ * cudaMalloc / cudaFree (nor any other allocating routine): its scratch is a static device
+ * array inside the library holding one partial maximum per patch, MHD_NOALLOC_MAX_PATCHES
+ * entries (128 KB of doubles plus a 4-byte counter), which every GPU that loads the
+ * library keeps until the process exits.
  *
  * Computes the same dt as mhd_bunch_cfl_dt (courant / max over interior cells of
  * sum_d (|u_d| + c_f,d)/dx_d) for `npatch` equal patches of nx*ny*nz active cells stored
@@ -282,15 +325,18 @@ const char *mhd_last_error(void);
  * active axes; ghost faces next to the interior must be filled).  Writes the double dt
  * to dt_dev (device memory) on cuda_stream (NULL: legacy default stream) without
  * synchronising.  real_bytes 4 or 8; npatch above MHD_NOALLOC_MAX_PATCHES is rejected
- * with MHD_EINVAL before any device work.  Cells whose rate is not finite are skipped
- * and not reported (the handle API reports them).
+ * with MHD_EINVAL before any device work.  A cell whose rate is not finite (non-physical
+ * state) makes the written dt NaN, so that a caller stepping with dt_dev on the device
+ * carries the failure forward instead of stepping with a dt that ignores the cell.
  *
- * Every call shares the one static array, which keeps the last call's contents (the
- * counter that must start at zero is cleared on the stream before each launch): calls
- * whose kernels may overlap on the GPU, e.g. on two streams at once, race and must be
- * ordered by the caller.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before any stream
- * capture begins. */
+ * cuda_stream must belong to the current device (MHD_EINVAL otherwise).  Every call shares
+ * the one static array, which keeps the last call's contents (the counter that must start
+ * at zero is cleared on the stream before each launch): calls whose kernels may overlap on
+ * the GPU, e.g. on two streams at once, race and must be ordered by the caller.  The first
+ * call on a device looks up the array's device address (with that device current; a
+ * lookup that fails is retried by the next call); make that first call before any stream
+ * capture begins.  A CUDA error already pending on the calling thread when the call starts
+ * is cleared, so that MHD_ECUDA reports this call's own failure. */
 #define MHD_NOALLOC_MAX_PATCHES 16384
 int mhd_cfl_dt_uniform_noalloc(const void *state, int real_bytes, int npatch, int nx, int ny,
                                int nz, int guard, const double dx[3], double gamma,

@@ -42,10 +42,12 @@ class MHDBunch:
     geom     workloads.Geometry (patch sizes, origins, box, dx, boundary kinds, guard)
     dtype    torch.float32 or torch.float64 (arithmetic precision of the kernels)
     riemann  face-flux solver: capi.MHD_RIEMANN_HLLD (default) or capi.MHD_RIEMANN_HLL
+    bind     allocate and bind the two device state buffers (False: the handle holds no
+             state on the device; only advance_out_of_core, which streams host state, runs)
     """
 
     def __init__(self, geom: Geometry, dtype=torch.float32, gamma=5.0 / 3.0, courant=0.8, limiter=0,
-                 device="cuda:0", stream: torch.cuda.Stream | None = None, riemann: int = 0):
+                 device="cuda:0", stream: torch.cuda.Stream | None = None, riemann: int = 0, bind: bool = True):
         if not torch.cuda.is_available():
             raise RuntimeError("MHDBunch needs a CUDA device (no CPU fallback)")
         self.lib = capi.load()
@@ -79,6 +81,9 @@ class MHDBunch:
                 raise RuntimeError("library state layout differs from the workload layout")
             self.nbytes = nbytes.value
             n = self.nbytes // self.rb
+            self.buf = None
+            if not bind:
+                return
             with torch.cuda.stream(self.stream):
                 self.buf = [torch.full((n,), float("nan"), dtype=dtype, device=self.device) for _ in range(2)]
             capi.check(self.lib.mhd_bunch_bind(h, ct.c_void_p(self.buf[0].data_ptr()),
@@ -137,6 +142,14 @@ class MHDBunch:
         """Face-flux solver of later steps: capi.MHD_RIEMANN_HLLD or capi.MHD_RIEMANN_HLL."""
         capi.check(self.lib.mhd_bunch_set_riemann(self.h, int(riemann)))
         self._params["riemann"] = int(riemann)
+
+    def set_bunches(self, bunches):
+        """Bunches (lists of patch indices covering every patch once) for MHD_MODE_BUNCH_LISTS."""
+        lists = [np.asarray(q, dtype=np.int32) for q in bunches]
+        patches = np.ascontiguousarray(np.concatenate(lists), dtype=np.int32)
+        starts = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(q) for q in lists])]), dtype=np.int32)
+        capi.check(self.lib.mhd_bunch_set_bunches(self.h, patches.ctypes.data_as(capi.I32P),
+                                                  starts.ctypes.data_as(capi.I32P), len(lists)))
 
     def set_mode(self, mode: int, config: int = -1):
         capi.check(self.lib.mhd_bunch_set_mode(self.h, int(mode), int(config)))
@@ -198,6 +211,22 @@ class MHDBunch:
         t = ct.c_double()
         capi.check(self.lib.mhd_bunch_advance_streamed_interior(self.h, ct.c_void_p(host_interior.data_ptr()), nsteps,
                                                                 nchunks, ct.byref(t)))
+        return t.value
+
+    def advance_out_of_core(self, host_state: torch.Tensor, host_scratch: torch.Tensor, nsteps: int,
+                            device_budget: int) -> float:
+        """nsteps steps of a host-resident state in the interior layout (pinned CPU tensors;
+        host_scratch of the same size is overwritten) using at most device_budget bytes of
+        device memory for the working set (mhd_bunch_advance_out_of_core); the new state is
+        in host_state; returns the simulated time."""
+        nb = self.interior_size()[0]
+        _check_buffer(host_state, self.dtype, nb, False, "host_state")
+        _check_buffer(host_scratch, self.dtype, nb, False, "host_scratch")
+        t = ct.c_double()
+        capi.check(self.lib.mhd_bunch_advance_out_of_core(self.h, ct.c_void_p(host_state.data_ptr()),
+                                                          ct.c_void_p(host_scratch.data_ptr()), int(nsteps),
+                                                          ct.c_size_t(int(device_budget)),
+                                                          ct.c_void_p(self.stream.cuda_stream), ct.byref(t)))
         return t.value
 
     def advance_async(self, t_span: float, max_rounds: int = 100000):

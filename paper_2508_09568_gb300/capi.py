@@ -16,7 +16,7 @@ MHD_OK, MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_EPHYS, MHD_EBOUNDS, MHD_ETIMEOUT,
 MHD_BC_PERIODIC, MHD_BC_OUTFLOW = 0, 1
 MHD_LIMITER_MINMOD, MHD_LIMITER_MC = 0, 1
 MHD_RIEMANN_HLLD, MHD_RIEMANN_HLL = 0, 1
-MHD_MODE_PER_PATCH, MHD_MODE_BUNCHED, MHD_MODE_PERSISTENT, MHD_MODE_MIXED = 0, 1, 2, 3
+MHD_MODE_PER_PATCH, MHD_MODE_BUNCHED, MHD_MODE_PERSISTENT, MHD_MODE_MIXED, MHD_MODE_BUNCH_LISTS = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "MHD_OK", -1: "MHD_EINVAL", -2: "MHD_ENOMEM", -3: "MHD_ECUDA", -4: "MHD_EPHYS",
                 -5: "MHD_EBOUNDS", -6: "MHD_ETIMEOUT", -7: "MHD_ESTATE"}
@@ -36,6 +36,7 @@ SIGNATURES = {
     "mhd_bunch_set_geometry": (I, [P, DP, I64P, I64P, I32P]),
     "mhd_bunch_set_params": (I, [P, D, D, I]),
     "mhd_bunch_set_riemann": (I, [P, I]),
+    "mhd_bunch_set_bunches": (I, [P, I32P, I32P, I]),
     "mhd_bunch_state_size": (I, [P, ct.POINTER(ct.c_size_t), I64P]),
     "mhd_bunch_bind": (I, [P, P, P, P]),
     "mhd_bunch_current": (I, [P, HP]),
@@ -55,6 +56,7 @@ SIGNATURES = {
     "mhd_bunch_advance_streamed": (I, [P, P, I, I, DP]),
     "mhd_bunch_interior_size": (I, [P, ct.POINTER(ct.c_size_t), I64P]),
     "mhd_bunch_advance_streamed_interior": (I, [P, P, I, I, DP]),
+    "mhd_bunch_advance_out_of_core": (I, [P, P, P, I, ct.c_size_t, P, DP]),
     "mhd_bunch_advance_async": (I, [P, D, I, ct.POINTER(I), I64P]),
     "mhd_bunch_async_round": (I, [P, I, I32P, DP, I, ct.POINTER(I)]),
     "mhd_bunch_step_adjoint": (I, [P, D, P, P, P]),

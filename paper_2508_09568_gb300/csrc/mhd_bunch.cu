@@ -36,27 +36,19 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
-// Catch clauses of every C entry point (a function-try-block): no exception crosses the
-// ABI; host allocation failures become MHD_ENOMEM, anything else MHD_EINVAL with its text.
-#define MHD_CATCH_ALL                                                                         \
-    catch (const std::bad_alloc&) {                                                           \
-        return fail(MHD_ENOMEM, "host memory allocation failed");                             \
-    }                                                                                         \
-    catch (const std::length_error&) {                                                        \
-        return fail(MHD_ENOMEM, "host allocation too large");                                 \
-    }                                                                                         \
-    catch (const std::exception& e_) {                                                        \
-        return fail(MHD_EINVAL, std::string("internal error: ") + e_.what());                 \
-    }                                                                                         \
-    catch (...) {                                                                             \
-        return fail(MHD_EINVAL, "internal error");                                            \
-    }
-
 #define CK(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
         if (e_ != cudaSuccess) return fail(MHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// smallest of n per-chunk time steps into *out (one warp)
+__global__ void min_dt_kernel(const double* __restrict__ v, int n, double* __restrict__ out) {
+    double m = v[0];
+    for (int i = threadIdx.x; i < n; i += 32) m = fmin(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = m;
+}
 
 // degenerate-star threshold of the HLLD solver, relative to Bn^2, per precision
 double hlld_eps(int rb) { return rb == 8 ? 1e-12 : 1e-6; }
@@ -157,6 +149,14 @@ struct mhd_bunch {
         int n = 0;
     };
     std::vector<MixedTiles> mixed;
+    // MHD_MODE_BUNCH_LISTS: the bunches of mhd_bunch_set_bunches (patch lists) and, per
+    // configuration, their tiles (each bunch's tiles longest first, bunches in list order)
+    std::vector<int> bunch_patches, bunch_start;
+    struct BunchTiles {
+        int4* d_tiles = nullptr;
+        std::vector<int> first, count;       // per bunch
+    };
+    std::vector<BunchTiles> btiles;
     // captured step sequences; with an odd step count the second starts from the other buffer
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -182,6 +182,11 @@ void free_mixed(mhd_bunch* b) {
     b->mixed.clear();
 }
 
+void free_btiles(mhd_bunch* b) {
+    for (auto& t : b->btiles) cudaFree(t.d_tiles);
+    b->btiles.clear();
+}
+
 void free_tiles(mhd_bunch* b) {
     for (auto& t : b->tiles) {
         cudaFree(t.d_nat);
@@ -189,6 +194,9 @@ void free_tiles(mhd_bunch* b) {
     }
     b->tiles.clear();
     free_mixed(b);
+    free_btiles(b);
+    b->bunch_patches.clear();
+    b->bunch_start.clear();
 }
 
 void release_graph(mhd_bunch* b) {
@@ -445,6 +453,21 @@ int do_step(mhd_bunch* b, const double* dt_ptr, double dt_val) {
         a.dynamic = 0;
         CK(L.launch(&a, T.n, b->stream));
         b->launches++;
+    } else if (b->mode == MHD_MODE_BUNCH_LISTS) {
+        // one persistent launch per bunch, in list order (each resets the work counter when
+        // its last CTA finishes, so the next one starts from zero)
+        if (b->btiles.empty()) return fail(MHD_ESTATE, "no bunch lists set (mhd_bunch_set_bunches)");
+        const auto& BT = b->btiles[k];
+        int occ = 1;
+        CK(L.occupancy(&occ));
+        occ = std::max(occ, 1);
+        for (size_t q = 0; q < BT.count.size(); ++q) {
+            a.tiles = BT.d_tiles + BT.first[q];
+            a.ntiles = BT.count[q];
+            a.dynamic = 1;
+            CK(L.launch(&a, std::min(BT.count[q], b->nsm * occ), b->stream));
+            b->launches++;
+        }
     } else if (b->mode == MHD_MODE_MIXED && !b->mixed.empty()) {
         // one persistent launch per configuration in use (each resets the work counter
         // when its last CTA finishes, so the next one starts from zero)
@@ -873,6 +896,47 @@ int mhd_bunch_set_riemann(mhd_bunch* b, int solver) try {
     return MHD_OK;
 } MHD_CATCH_ALL
 
+int mhd_bunch_set_bunches(mhd_bunch* b, const int32_t* patches, const int32_t* starts, int nbunch) try {
+    if (!b || !patches || !starts) return fail(MHD_EINVAL, "NULL argument");
+    if (!b->have_geom) return fail(MHD_ESTATE, "set_geometry first");
+    if (nbunch < 1 || nbunch > b->npatch) return fail(MHD_EINVAL, "nbunch must be in 1..npatch");
+    if (starts[0] != 0 || starts[nbunch] != b->npatch)
+        return fail(MHD_EINVAL, "starts must run from 0 to npatch");
+    std::vector<char> seen(b->npatch, 0);
+    for (int q = 0; q < nbunch; ++q) {
+        if (starts[q + 1] <= starts[q]) return fail(MHD_EINVAL, "every bunch must hold at least one patch");
+        for (int i = starts[q]; i < starts[q + 1]; ++i) {
+            const int p = patches[i];
+            if (p < 0 || p >= b->npatch || seen[p]) return fail(MHD_EINVAL, "patches must list every patch once");
+            seen[p] = 1;
+        }
+    }
+    release_graph(b);
+    free_btiles(b);
+    b->bunch_patches.assign(patches, patches + b->npatch);
+    b->bunch_start.assign(starts, starts + nbunch + 1);
+    b->btiles.resize(b->tiles.size());
+    for (size_t k = 0; k < b->tiles.size(); ++k) {
+        const auto& T = b->tiles[k];
+        auto& BT = b->btiles[k];
+        std::vector<int4> all;
+        for (int q = 0; q < nbunch; ++q) {
+            std::vector<int4> tl;
+            for (int i = starts[q]; i < starts[q + 1]; ++i) {
+                const int p = patches[i];
+                tl.insert(tl.end(), T.nat_h.begin() + T.first[p], T.nat_h.begin() + T.first[p] + T.count[p]);
+            }
+            std::stable_sort(tl.begin(), tl.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+            BT.first.push_back((int)all.size());
+            BT.count.push_back((int)tl.size());
+            all.insert(all.end(), tl.begin(), tl.end());
+        }
+        CK(cudaMalloc(&BT.d_tiles, sizeof(int4) * all.size()));
+        CK(cudaMemcpy(BT.d_tiles, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
+    }
+    return MHD_OK;
+} MHD_CATCH_ALL
+
 int mhd_bunch_interior_size(const mhd_bunch* b, size_t* bytes, int64_t* patch_offsets) try {
     if (!b || !bytes) return fail(MHD_EINVAL, "NULL argument");
     int64_t o = 0;
@@ -959,7 +1023,7 @@ int mhd_bunch_step_device_dt(mhd_bunch* b, const void* dt_dev) try {
 
 int mhd_bunch_set_mode(mhd_bunch* b, int mode, int config) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
-    if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_MIXED) return fail(MHD_EINVAL, "bad mode");
+    if (mode < MHD_MODE_PER_PATCH || mode > MHD_MODE_BUNCH_LISTS) return fail(MHD_EINVAL, "bad mode");
     if (config < -1 || config >= (int)b->cfg_index.size()) return fail(MHD_EINVAL, "bad config index");
     release_graph(b);
     b->mode = mode;
@@ -1325,6 +1389,255 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
     b->cur = B;
     std::vector<double> dts(nsteps);
     CK(cudaMemcpyAsync(dts.data(), b->d_dts, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, b->stream));
+    int code = 0;
+    rc = read_error(b, &code, nullptr, 0);
+    if (rc) return rc;
+    if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
+    return code;
+} MHD_CATCH_ALL
+
+int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scratch, int nsteps,
+                                  size_t device_budget, void* cuda_stream, double* t_out) try {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (!b->have_geom) return fail(MHD_ESTATE, "mhd_bunch_set_geometry has not been called");
+    if (!host_state || !host_scratch || host_state == host_scratch || nsteps < 1 || device_budget == 0)
+        return fail(MHD_EINVAL, "bad argument");
+    if (b->ndim != 3) return fail(MHD_EINVAL, "the out-of-core advance needs a 3D box");
+    if (b->cfg_index.empty()) return fail(MHD_EINVAL, "no compiled kernel for this dimensionality");
+    const int P = b->npatch;
+    const int nx = b->pn[0], ny = b->pn[1], nz = b->pn[2];
+    int64_t np3[3];
+    for (int d = 0; d < 3; ++d) np3[d] = b->domain[d] / b->pn[d];
+    const int64_t ppl = np3[0] * np3[1];
+    const int NL = (int)np3[2];
+    bool grid = ppl * NL == P;
+    for (int p = 0; p < P && grid; ++p) {
+        grid = b->pn[3 * p] == nx && b->pn[3 * p + 1] == ny && b->pn[3 * p + 2] == nz &&
+               b->origin[3 * p] == (p % np3[0]) * nx && b->origin[3 * p + 1] == ((p / np3[0]) % np3[1]) * ny &&
+               b->origin[3 * p + 2] == (p / ppl) * nz;
+    }
+    if (!grid) return fail(MHD_EINVAL, "the out-of-core advance needs equal patches on a grid, x fastest in patch order");
+    const PatchDev& h0 = b->hp[0];
+    const int64_t pe = 8LL * h0.X * h0.Y * h0.Z;           // elements of a padded patch
+    const int64_t ie = 8LL * nx * ny * nz;                 // elements of a patch's interior
+    if (pe * (b->rb / 4) >= ((int64_t)1 << 31))
+        return fail(MHD_EINVAL, "a patch is too large for the interior-layout copies (2^31 words)");
+    const size_t PL = (size_t)(ppl * pe * b->rb), IL = (size_t)(ppl * ie * b->rb);   // bytes per layer
+    // the largest chunk of L layers whose working set fits: a ring of L+2 padded layers
+    // (the chunk and one layer above and below it) for U^n and one for U^{n+1}, two
+    // single-layer upload stages, two chunk download stages, tables
+    auto need = [&](int L) {
+        const size_t tab = (size_t)L * ppl * (sizeof(PatchDev) + 27 * sizeof(int64_t) + 16 + (size_t)h0.Z * b->rb);
+        return 2 * (size_t)(L + 2) * PL + 2 * IL + 2 * (size_t)L * IL + (size_t)(L + 2) * ppl * sizeof(PatchDev) + tab +
+               (1 << 20);
+    };
+    int L = NL;
+    while (L > 0 && need(L) > device_budget) --L;
+    if (L == 0)
+        return fail(MHD_ENOMEM, "device_budget too small: one layer of patches needs " + std::to_string(need(1)) +
+                                    " bytes");
+    const int K = (NL + L - 1) / L;
+    const int S = L + 2;                                   // ring slots (layers)
+    auto slot = [&](int g) { return ((g % S) + S) % S; };  // g: unwrapped layer index in [-1, NL]
+    const bool zper_lo = b->bc[4] == MHD_BC_PERIODIC, zper_hi = b->bc[5] == MHD_BC_PERIODIC;
+    const int k = b->config < 0 ? default_config(b) : b->config;
+    const StepLaunch& SL = step_cfg(b, k);
+    const auto& T = b->tiles[k];
+    int occ = 1;
+    CK(SL.occupancy(&occ));
+    occ = std::max(occ, 1);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int rc = ensure_stream_pipeline(b, 4);
+    if (rc) return rc;
+    // ---- host tables: ring slots (scatter / gather), chunks (fill, CFL, update)
+    std::vector<PatchDev> slot_tab((size_t)S * ppl);
+    for (int sl = 0; sl < S; ++sl)
+        for (int64_t j = 0; j < ppl; ++j) {
+            PatchDev q = h0;
+            q.off = ((int64_t)sl * ppl + j) * pe;
+            slot_tab[(size_t)sl * ppl + j] = q;
+        }
+    std::vector<int64_t> ioff_layer(ppl);
+    for (int64_t j = 0; j < ppl; ++j) ioff_layer[j] = j * ie;
+    std::vector<PatchDev> ctab;
+    std::vector<int64_t> cnb;
+    std::vector<int4> ctiles;
+    std::vector<int> cfirst(K), cnp(K), ctfirst(K), ctn(K);
+    for (int c = 0; c < K; ++c) {
+        const int z0 = c * L, z1 = std::min(NL, z0 + L);
+        cfirst[c] = (int)ctab.size();
+        cnp[c] = (int)((z1 - z0) * ppl);
+        ctfirst[c] = (int)ctiles.size();
+        for (int g = z0; g < z1; ++g)
+            for (int64_t j = 0; j < ppl; ++j) {
+                const int p = (int)(g * ppl + j);
+                PatchDev q = b->hp[p];
+                q.off = ((int64_t)slot(g) * ppl + j) * pe;
+                const int local = (int)ctab.size() - cfirst[c];
+                ctab.push_back(q);
+                const int64_t ix = j % np3[0], iy = j / np3[0];
+                for (int sz = -1; sz <= 1; ++sz)
+                    for (int sy = -1; sy <= 1; ++sy)
+                        for (int sx = -1; sx <= 1; ++sx) {
+                            // neighbour in the ring: same layer (x, y wrapped), or the layer
+                            // above / below; across an outflow box face the guard fill never
+                            // reads it (clamped to the patch itself)
+                            const int64_t jx = ((ix + sx) % np3[0] + np3[0]) % np3[0];
+                            const int64_t jy = ((iy + sy) % np3[1] + np3[1]) % np3[1];
+                            int gz = g + sz;
+                            if ((gz < 0 && !zper_lo) || (gz >= NL && !zper_hi)) gz = g;
+                            cnb.push_back(((int64_t)slot(gz) * ppl + jy * np3[0] + jx) * pe);
+                        }
+                for (int t = T.first[p]; t < T.first[p] + T.count[p]; ++t) {
+                    int4 tl = T.nat_h[t];
+                    tl.x = local;
+                    ctiles.push_back(tl);
+                }
+            }
+        std::stable_sort(ctiles.begin() + ctfirst[c], ctiles.end(), [](const int4& x, const int4& y) { return x.w > y.w; });
+        ctn[c] = (int)ctiles.size() - ctfirst[c];
+    }
+    // ---- device working set (released on return)
+    struct Mem {
+        std::vector<void*> v;
+        ~Mem() {
+            for (void* x : v) cudaFree(x);
+        }
+        void* get(size_t n) {
+            void* x = nullptr;
+            if (cudaMalloc(&x, n) != cudaSuccess) return nullptr;
+            v.push_back(x);
+            return x;
+        }
+    } mem;
+    char* ring = static_cast<char*>(mem.get((size_t)S * PL));
+    char* ring_new = static_cast<char*>(mem.get((size_t)S * PL));
+    char* in_stage[2] = {static_cast<char*>(mem.get(IL)), static_cast<char*>(mem.get(IL))};
+    char* out_stage[2] = {static_cast<char*>(mem.get((size_t)L * IL)), static_cast<char*>(mem.get((size_t)L * IL))};
+    PatchDev* d_slot = static_cast<PatchDev*>(mem.get(sizeof(PatchDev) * slot_tab.size()));
+    int64_t* d_ioff = static_cast<int64_t*>(mem.get(sizeof(int64_t) * ppl));
+    PatchDev* d_ctab = static_cast<PatchDev*>(mem.get(sizeof(PatchDev) * ctab.size()));
+    int64_t* d_cnb = static_cast<int64_t*>(mem.get(sizeof(int64_t) * cnb.size()));
+    int4* d_ctiles = static_cast<int4*>(mem.get(sizeof(int4) * ctiles.size()));
+    void* d_part = mem.get((size_t)L * ppl * h0.Z * b->rb);
+    unsigned* d_cnt = static_cast<unsigned*>(mem.get(sizeof(unsigned)));
+    double* d_cdt = static_cast<double*>(mem.get(sizeof(double) * K));
+    double* d_dts = static_cast<double*>(mem.get(sizeof(double) * nsteps));
+    for (void* x : {(void*)ring, (void*)ring_new, (void*)in_stage[0], (void*)in_stage[1], (void*)out_stage[0],
+                    (void*)out_stage[1], (void*)d_slot, (void*)d_ioff, (void*)d_ctab, (void*)d_cnb, (void*)d_ctiles,
+                    d_part, (void*)d_cnt, (void*)d_cdt, (void*)d_dts})
+        if (!x) return fail(MHD_ENOMEM, "cudaMalloc of the out-of-core working set failed");
+    CK(cudaMemcpy(d_slot, slot_tab.data(), sizeof(PatchDev) * slot_tab.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_ioff, ioff_layer.data(), sizeof(int64_t) * ppl, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_ctab, ctab.data(), sizeof(PatchDev) * ctab.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_cnb, cnb.data(), sizeof(int64_t) * cnb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_ctiles, ctiles.data(), sizeof(int4) * ctiles.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_cnt, 0, sizeof(unsigned)));
+    // ---- host buffers: step s reads hbuf[r] and writes hbuf[1 - r]; the last step writes
+    // host_state (an odd step count starts from a copy in host_scratch)
+    char* hbuf[2] = {static_cast<char*>(host_state), static_cast<char*>(host_scratch)};
+    int r = 0;
+    if (nsteps % 2) {
+        std::memcpy(hbuf[1], hbuf[0], (size_t)P * ie * b->rb);
+        r = 1;
+    }
+    double dxi[3];
+    int act[3];
+    for (int d = 0; d < 3; ++d) {
+        dxi[d] = 1.0 / b->dx[d];
+        act[d] = active(b, d);
+    }
+    const int wpr = b->rb / 4;
+    cudaEvent_t ev_up[2] = {b->ev_in[0], b->ev_in[1]}, ev_sc[2] = {b->ev_step[0], b->ev_step[1]};
+    cudaEvent_t ev_ga[2] = {b->ev_in[2], b->ev_in[3]}, ev_dn[2] = {b->ev_out[0], b->ev_out[1]};
+    cudaEvent_t ev_go = b->ev_step[2], ev_done = b->ev_out[2];
+    int64_t nup = 0, ndown = 0;
+    // the copy streams start after the work already queued on st
+    CK(cudaEventRecord(ev_go, st));
+    CK(cudaStreamWaitEvent(b->s_in, ev_go, 0));
+    CK(cudaStreamWaitEvent(b->s_out, ev_go, 0));
+    // layer g (unwrapped) of the read buffer into its ring slot: upload into a stage (copy
+    // stream), scatter on st
+    auto upload = [&](const char* hsrc, int g) -> int {
+        const int gs = ((g % NL) + NL) % NL;
+        const int u = (int)(nup++ % 2);
+        CK(cudaStreamWaitEvent(b->s_in, ev_sc[u], 0));
+        CK(cudaMemcpyAsync(in_stage[u], hsrc + (size_t)gs * IL, IL, cudaMemcpyHostToDevice, b->s_in));
+        CK(cudaEventRecord(ev_up[u], b->s_in));
+        CK(cudaStreamWaitEvent(st, ev_up[u], 0));
+        interior_copy_kernel<<<dim3(nz, (unsigned)ppl), 256, 0, st>>>(
+            reinterpret_cast<unsigned*>(ring), reinterpret_cast<unsigned*>(in_stage[u]), d_slot + (size_t)slot(g) * ppl,
+            d_ioff, 0, (int)ppl, wpr, 1);
+        ++b->launches;
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ev_sc[u], st));
+        return MHD_OK;
+    };
+    // the layers of chunk c's window not left in the ring by chunk c-1
+    auto load_window = [&](const char* hsrc, int c) -> int {
+        const int z0 = c * L, z1 = std::min(NL, z0 + L);
+        const int lo = c == 0 ? z0 - 1 : z0 + 1;
+        for (int g = lo; g <= z1; ++g) {
+            if ((g < 0 && !zper_lo) || (g >= NL && !zper_hi)) continue;
+            const int e = upload(hsrc, g);
+            if (e) return e;
+        }
+        return MHD_OK;
+    };
+    for (int s = 0; s < nsteps; ++s) {
+        const char* R = hbuf[r];
+        char* W = hbuf[1 - r];
+        // the previous step's downloads (into the buffer read now) come first
+        CK(cudaStreamWaitEvent(b->s_in, ev_done, 0));
+        // pass 1: guard fill + CFL rates of every chunk; dt = the smallest chunk dt
+        for (int c = 0; c < K; ++c) {
+            if ((rc = load_window(R, c))) return rc;
+            CK(b->K->fill_cfl(ring, d_ctab + cfirst[c], cnp[c], d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->gamma,
+                              b->courant, dxi, act, d_part, d_cnt, d_cdt + c, b->d_err, st));
+            ++b->launches;
+        }
+        min_dt_kernel<<<1, 32, 0, st>>>(d_cdt, K, d_dts + s);
+        ++b->launches;
+        CK(cudaGetLastError());
+        // pass 2: guard fill, update, gather and download of every chunk
+        for (int c = 0; c < K; ++c) {
+            if ((rc = load_window(R, c))) return rc;
+            CK(b->K->fill(ring, d_ctab + cfirst[c], cnp[c], b->fg, d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->d_err, st));
+            ++b->launches;
+            StepHostArgs a = step_args(b, d_dts + s, 0.0);
+            a.U = ring;
+            a.Unew = ring_new;
+            a.patches = d_ctab + cfirst[c];
+            a.tiles = d_ctiles + ctfirst[c];
+            a.ntiles = ctn[c];
+            a.dynamic = 1;
+            CK(SL.launch(&a, std::min(ctn[c], b->nsm * occ), st));
+            ++b->launches;
+            const int o = (int)(ndown++ % 2);
+            CK(cudaStreamWaitEvent(st, ev_dn[o], 0));
+            const int z0 = c * L, z1 = std::min(NL, z0 + L);
+            for (int g = z0; g < z1; ++g) {
+                interior_copy_kernel<<<dim3(nz, (unsigned)ppl), 256, 0, st>>>(
+                    reinterpret_cast<unsigned*>(ring_new), reinterpret_cast<unsigned*>(out_stage[o] + (size_t)(g - z0) * IL),
+                    d_slot + (size_t)slot(g) * ppl, d_ioff, 0, (int)ppl, wpr, 0);
+                ++b->launches;
+                CK(cudaGetLastError());
+            }
+            CK(cudaEventRecord(ev_ga[o], st));
+            CK(cudaStreamWaitEvent(b->s_out, ev_ga[o], 0));
+            CK(cudaMemcpyAsync(W + (size_t)z0 * IL, out_stage[o], (size_t)(z1 - z0) * IL, cudaMemcpyDeviceToHost,
+                               b->s_out));
+            CK(cudaEventRecord(ev_dn[o], b->s_out));
+        }
+        CK(cudaEventRecord(ev_done, b->s_out));
+        r = 1 - r;
+    }
+    CK(cudaStreamWaitEvent(st, ev_done, 0));
+    std::vector<double> dts(nsteps);
+    CK(cudaMemcpyAsync(dts.data(), d_dts, sizeof(double) * nsteps, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaStreamSynchronize(b->s_in));
+    CK(cudaStreamSynchronize(b->s_out));
     int code = 0;
     rc = read_error(b, &code, nullptr, 0);
     if (rc) return rc;

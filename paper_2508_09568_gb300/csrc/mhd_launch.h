@@ -4,7 +4,28 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <new>
+#include <stdexcept>
+#include <string>
+
 #include "mhd_common.cuh"
+
+// Catch clauses of every C entry point (a function-try-block; the translation unit defines
+// fail(code, message)): no exception crosses the ABI; host allocation failures become
+// MHD_ENOMEM, anything else MHD_EINVAL with its text.
+#define MHD_CATCH_ALL                                                                         \
+    catch (const std::bad_alloc&) {                                                           \
+        return fail(MHD_ENOMEM, "host memory allocation failed");                             \
+    }                                                                                         \
+    catch (const std::length_error&) {                                                        \
+        return fail(MHD_ENOMEM, "host allocation too large");                                 \
+    }                                                                                         \
+    catch (const std::exception& e_) {                                                        \
+        return fail(MHD_EINVAL, std::string("internal error: ") + e_.what());                 \
+    }                                                                                         \
+    catch (...) {                                                                             \
+        return fail(MHD_EINVAL, "internal error");                                            \
+    }
 
 namespace mhd {
 

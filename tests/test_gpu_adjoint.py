@@ -304,6 +304,122 @@ def test_rollout_gradient_of_adjoint_workload():
         assert abs(float(fd - an)) <= 2e-3 * abs(float(an)), (float(fd), float(an))
 
 
+def _switch_codes(U, geom, gamma):
+    """Branch choices of the step on a filled state (flat tensor on the GPU): for every cell
+    with a full stencil, primitive and axis, the limiter's choice (0: slopes of opposite
+    sign, 1: the left difference, 2: the right one); and for every face, which neighbour has
+    the larger normal velocity and the larger fast speed -- the choices of the HLLD wave
+    speed estimates, taken on the cell-centred time-n states as a stand-in for the face
+    states the kernel uses."""
+    Z, Y, X = geom.padded(0)
+    V = U.view(geom.npatch, 8, Z, Y, X)
+    c = (slice(None), slice(0, Z - 1), slice(0, Y - 1), slice(0, X - 1))
+    rho = V[:, 0][c]
+    vel = [V[:, 1 + d][c] / rho for d in range(3)]
+    bc = [0.5 * (V[:, 5][c] + V[:, 5][:, :-1, :-1, 1:]), 0.5 * (V[:, 6][c] + V[:, 6][:, :-1, 1:, :-1]),
+          0.5 * (V[:, 7][c] + V[:, 7][:, 1:, :-1, :-1])]
+    P = (gamma - 1) * (V[:, 4][c] - 0.5 * rho * sum(v * v for v in vel) - 0.5 * sum(b * b for b in bc))
+    prims = [rho] + vel + [P] + bc
+    codes = []
+    for d in range(3):
+        ax = 3 - d
+        for q in prims:
+            n = q.shape[ax]
+            a = q.narrow(ax, 1, n - 2) - q.narrow(ax, 0, n - 2)
+            b = q.narrow(ax, 2, n - 2) - q.narrow(ax, 1, n - 2)
+            codes.append(torch.where(a * b > 0, torch.where(a.abs() <= b.abs(), 1, 2), 0).to(torch.int8))
+        cs2 = gamma * P / rho
+        b2 = sum(x * x for x in bc) / rho
+        bn2 = bc[d] * bc[d] / rho
+        cf = torch.sqrt(0.5 * (cs2 + b2 + torch.sqrt(torch.clamp((cs2 + b2) ** 2 - 4 * cs2 * bn2, min=0))))
+        n = rho.shape[ax]
+        for q in (vel[d], cf):
+            codes.append((q.narrow(ax, 1, n - 1) >= q.narrow(ax, 0, n - 1)).to(torch.int8))
+    return codes
+
+
+def test_rollout_fd_discrepancy_follows_branch_switches():
+    """Where the 200-step finite-difference discrepancy of the adjoint workload comes from.
+    Along one direction, central differences at h = 1e-6, 1e-7, 1e-8 are compared with the
+    gradient while the limiter and wave-speed choices of the two runs U0 +- h d are compared
+    at every step (switches at the first step counted apart):
+      * from the workload's own initial state (uniform pressure and B_z = 0: every slope of
+        P and B_z is a tie at the first step, sitting on the limiter's kink), the first-step
+        switches do not fall with h (about 8.2e5 at every h) and the discrepancy levels off
+        near 1.3e-4 -- the difference quotient measures one-sided slopes there, the adjoint
+        the subgradient;
+      * from the same state with seeded noise on every interior entry (no ties), the
+        switches of every step fall tenfold per decade of h and the discrepancy with them
+        (1.1e-3, 1.4e-4, 3.3e-5 at h = 1e-6, 1e-7, 1e-8).
+    Counts and errors are printed (-s) for the record."""
+    from paper_2508_09568_gb300.autograd import rollout
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, state_of, v0, vt, meta, bunch, dt, dmask = _workload()
+    gamma = meta["gamma"]
+    steps, ck = meta["steps"], meta["ckpt"]
+    zero = torch.zeros((), dtype=torch.float64, device="cuda")
+    m = interior_mask(geom)
+    with torch.no_grad():
+        target = rollout(state_of(torch.tensor(vt, device="cuda")), bunch, dt, steps, ck)
+        base = state_of(torch.tensor(v0, device="cuda"))
+        starts = {"workload state": base,
+                  "jittered state": torch.tensor(jitter(base.cpu().numpy(), m, 21), device="cuda")}
+    rng = np.random.default_rng(3)
+    d = torch.where(torch.tensor(m, device="cuda"), torch.tensor(rng.normal(size=m.size), device="cuda"), zero)
+    runs = [MHDBunch(geom, dtype=torch.float64, gamma=gamma) for _ in range(2)]
+    lim_idx = [q * 10 + k for q in range(3) for k in range(8)]
+    ws_idx = [q * 10 + k for q in range(3) for k in (8, 9)]
+
+    def loss_of(U):
+        return torch.sum(torch.where(dmask, (U - target) ** 2, zero))
+
+    def pair(U0, h):
+        """the two runs U0 +- h d in lockstep: their final losses and the number of choices
+        that differ between them (first step, later steps)"""
+        for r, sgn in zip(runs, (1.0, -1.0)):
+            r.current().copy_(U0 + sgn * h * d)
+        torch.cuda.synchronize()
+        first = later = 0
+        for k in range(steps):
+            for r in runs:
+                r.fill_guards()
+                r.stream.synchronize()
+            cp, cm = (_switch_codes(r.current(), geom, gamma) for r in runs)
+            n = sum(int((cp[i] != cm[i]).sum()) for i in lim_idx + ws_idx)
+            if k == 0:
+                first += n
+            else:
+                later += n
+            torch.cuda.synchronize()
+            for r in runs:
+                r.step(dt)
+        for r in runs:
+            r.stream.synchronize()
+        return float(loss_of(runs[0].current())), float(loss_of(runs[1].current())), first, later
+
+    res = {}
+    for name, U0 in starts.items():
+        U = U0.clone().requires_grad_(True)
+        loss_of(rollout(U, bunch, dt, steps, ck)).backward()
+        an = float(torch.sum(U.grad.detach() * d))
+        res[name] = []
+        for h in (1e-6, 1e-7, 1e-8):
+            with torch.no_grad():
+                lp, lm, first, later = pair(U0, h)
+            res[name].append((h, first, later, abs((lp - lm) / (2 * h) - an) / abs(an)))
+    for r in runs:
+        r.close()
+    print("\nstart, h, switches at step 1, switches at steps 2..200, |fd - adjoint| / |adjoint|")
+    for name, rows in res.items():
+        for r in rows:
+            print("%-15s %.0e %9d %9d %.3e" % ((name,) + r))
+    w, j = res["workload state"], res["jittered state"]
+    assert w[2][1] > 0.5 * w[0][1]                   # ties: first-step switches at any h
+    assert 4 * w[2][2] < w[0][2] and 4 * j[2][2] < j[0][2] and 4 * j[2][1] < j[0][1] + 4
+    assert w[2][3] <= 2e-3
+    assert j[2][3] < 0.1 * j[0][3]                   # no ties: the discrepancy falls with h
+
+
 def test_rollout_gradient_short_horizon_fd_1e6():
     """Two checkpointed steps of the adjoint workload from its initial state with seeded noise
     on every interior entry (a point where the step is differentiable with margin: no exactly

@@ -61,6 +61,37 @@ def test_ragged_small_fill_and_modes():
         assert np.array_equal(o, outs[0])
 
 
+def test_bunch_lists_equal_one_launch():
+    """MHD_MODE_BUNCH_LISTS (one persistent launch per bunch, the paper's bunches of
+    patches) gives bitwise the state of the single persistent launch, with one launch per
+    bunch; bad lists are rejected and change nothing."""
+    geom, U, meta = W.ragged_small()
+    flat = W.to_patches(U, geom)
+    rng = np.random.default_rng(11)
+    perm = rng.permutation(geom.npatch)
+    cuts = np.sort(rng.choice(np.arange(1, geom.npatch), 3, replace=False))
+    bunches = np.split(perm, cuts)
+    for dtype in (torch.float64, torch.float32):
+        b = gpu_bunch(geom, flat, meta["gamma"], dtype)
+        b.set_mode(capi.MHD_MODE_PERSISTENT, 0)
+        ref = interior_global(gpu_steps(b, [2e-3, 2e-3]), geom)
+        with pytest.raises(capi.MHDError):
+            b.set_bunches([perm[:-1]])                 # a patch missing
+        with pytest.raises(capi.MHDError):
+            b.set_bunches([perm, perm[:1]])            # a patch twice
+        b.set_mode(capi.MHD_MODE_BUNCH_LISTS, 0)
+        with pytest.raises(capi.MHDError) as ei:       # no bunches yet
+            gpu_steps(b, [2e-3])
+        assert ei.value.code == capi.MHD_ESTATE
+        b.set_bunches(bunches)
+        b.upload(flat)
+        n0 = b.launch_count()
+        got = interior_global(gpu_steps(b, [2e-3, 2e-3]), geom)
+        assert b.launch_count() - n0 == 2 * (1 + len(bunches))   # fill + one launch per bunch, per step
+        assert np.array_equal(got, ref)
+        b.close()
+
+
 def test_ragged_box_full_size_sampled_and_invariants():
     from paper_2508_09568_gb300.bunch import MHDBunch
     geom, fields, meta = W.ragged_box()

@@ -85,3 +85,62 @@ def test_streamed_chunks_cut_at_whole_waves():
         assert np.array_equal(W.from_interior(hi.numpy().astype(np.float64), geom), want)
     code, msg = b.error()
     assert code == 0, msg
+
+
+def _tall_box(bcz):
+    """A 32 x 32 x 512 box of sixteen 32^3 patches stacked along z (one patch per layer),
+    seeded smooth fields; z boundaries periodic or outflow."""
+    g0, U, meta = W.small_box(ncell=(32, 32, 512), patch=(32, 32, 32), seed=47)
+    bc = [[W.BC_PERIODIC, W.BC_PERIODIC], [W.BC_PERIODIC, W.BC_PERIODIC], [bcz, bcz]]
+    return W.uniform_geometry([32, 32, 512], [32, 32, 32], dx=g0.dx, bc=bc), U, meta
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("bcz", ["periodic", "outflow"])
+def test_out_of_core_equals_device_resident(dtype, bcz):
+    """mhd_bunch_advance_out_of_core on a handle with no device state, its working set
+    capped below the size of the host state (so that the state cannot be held on the device
+    at once): three steps equal, bitwise, the same steps run on the device-resident state
+    (fused guard fill + CFL dt, then the update), interior and simulated time; likewise with
+    budgets that take three layers per chunk (the last chunk shorter) and the whole box."""
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, U, meta = _tall_box(W.BC_PERIODIC if bcz == "periodic" else W.BC_OUTFLOW)
+    npd = np.float64 if dtype == torch.float64 else np.float32
+    flat = rounded(W.to_patches(U, geom), dtype)
+    ref = MHDBunch(geom, dtype=dtype, gamma=meta["gamma"])
+    ref.upload(flat)
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t_ref = 0.0
+    for _ in range(3):
+        ref.fill_cfl_device(dt_dev)
+        ref.step_device_dt(dt_dev)
+        ref.stream.synchronize()
+        t_ref += float(dt_dev.item())
+    want = W.from_patches(ref.download().astype(np.float64), geom)
+    code, msg = ref.error()
+    assert code == 0, msg
+    ref.close()
+    ooc = MHDBunch(geom, dtype=dtype, gamma=meta["gamma"], bind=False)
+    host_bytes = ooc.interior_size()[0]
+    rb = 8 if dtype == torch.float64 else 4
+    layer_padded = 8 * 38 ** 3 * rb
+    for budget in (host_bytes - 1, 2 * 5 * layer_padded + 8 * 32 ** 3 * 8 * rb + (2 << 20), 1 << 34):
+        host = torch.tensor(W.to_interior(rounded(W.from_patches(flat, geom), dtype), geom, dtype=npd)).pin_memory()
+        scratch = torch.empty_like(host).pin_memory()
+        t = ooc.advance_out_of_core(host, scratch, 3, budget)
+        assert t == t_ref, budget
+        got = W.from_interior(host.numpy().astype(np.float64), geom)
+        assert np.array_equal(got, want), budget
+    ooc.close()
+
+
+def test_out_of_core_rejects_a_budget_below_one_layer():
+    from paper_2508_09568_gb300 import capi
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    geom, U, meta = _tall_box(W.BC_PERIODIC)
+    ooc = MHDBunch(geom, dtype=torch.float32, gamma=meta["gamma"], bind=False)
+    host = torch.zeros(ooc.interior_size()[0] // 4, dtype=torch.float32).pin_memory()
+    with pytest.raises(capi.MHDError) as ei:
+        ooc.advance_out_of_core(host, host.clone(), 1, 1 << 20)
+    assert ei.value.code == capi.MHD_ENOMEM
+    ooc.close()

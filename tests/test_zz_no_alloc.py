@@ -1,8 +1,8 @@
 """The allocation-free CFL entry point agrees with the handle-based one.
 
-mhd_cfl_dt_uniform_noalloc serves callers that may not allocate device memory (a stream
-under graph capture, a host framework that owns all device memory, a real-time loop): it
-needs no handle and keeps its scratch in a static device array of the library.  Here it
+mhd_cfl_dt_uniform_noalloc serves callers that may not allocate device memory (a host
+framework that owns and accounts for all device memory, a real-time loop): it needs no
+handle and keeps its scratch in a static device array of the library.  Here it
 is called through the C ABI, twice in a row on the same state and then on a second, smaller
 bunch, and each result is checked against mhd_bunch_cfl_dt on the same data, within the
 tolerances of the other CFL tests.  This file is collected last on purpose.
@@ -63,3 +63,30 @@ def test_noalloc_rejects_too_many_patches():
                                         3, dx, 5.0 / 3.0, 0.8, ct.c_void_p(dummy.data_ptr()), None)
     assert rc == capi.MHD_EINVAL
     assert b"MHD_NOALLOC_MAX_PATCHES" in lib.mhd_last_error()
+
+
+def test_noalloc_reports_a_nonphysical_cell_as_nan():
+    """A cell with a negative density has no finite rate: the written dt is NaN (the
+    handle API latches MHD_EPHYS for the same state), and the next call on a healthy
+    state writes the finite dt again (the static array keeps no stale flag)."""
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    lib = capi.load()
+    geom, U, meta = W.small_box(ncell=(16, 16, 16), patch=(8, 8, 8), seed=34)
+    b = MHDBunch(geom, dtype=torch.float64, gamma=meta["gamma"], courant=0.8)
+    b.upload(W.to_patches(U, geom))
+    b.fill_guards()
+    ref = b.cfl_dt()
+    bad = U.copy()
+    bad[0, 3, 4, 5] = -1.0
+    b2 = MHDBunch(geom, dtype=torch.float64, gamma=meta["gamma"], courant=0.8)
+    b2.upload(W.to_patches(bad, geom))
+    b2.fill_guards()
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    capi.check(_noalloc(lib, b2.current(), 8, geom, meta["gamma"], 0.8, dt_dev, b2.stream))
+    b2.stream.synchronize()
+    assert np.isnan(float(dt_dev.item()))
+    capi.check(_noalloc(lib, b.current(), 8, geom, meta["gamma"], 0.8, dt_dev, b.stream))
+    b.stream.synchronize()
+    assert abs(float(dt_dev.item()) - ref) <= TOL[torch.float64] * ref
+    b.close()
+    b2.close()
