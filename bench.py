@@ -7,10 +7,13 @@ seeded solenoidal velocity with E(k) ~ k^-2 over 1 <= |k| <= 8 and rms Mach 1, F
 One step = guard fill + CFL dt on the device (one pass) + fused update (persistent
 kernel), the sequence captured in a CUDA graph.  Metric: 3D MHD cell-updates per second.
 
-Prints ONE JSON line (rank 0).  Under torchrun every rank runs an independent replica of
-the box on its own GPU (the box is not split across GPUs: replicas only), and value is
-the total over ranks.  --impl reference times the FP64 CPU oracle on the host cores on a
-bounded sample of the same workload.
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) the box is repeated N times along z
+and split into one slab of patch layers per GPU (domain.SlabDomain): per step one patch
+layer goes each way between neighbouring ranks (NCCL send/recv) and the dt is the minimum
+over ranks (all_reduce); per-GPU work is that of N = 1 (weak scaling) and value counts the
+cells of all slabs.  The other legs (per-kernel times, end to end, plain path) run on each
+rank's own copy of the N = 1 box.  --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -37,6 +40,7 @@ FLOPS_PER_CELL = 3255.0
 BYTES_PER_CELL = {4: 64.0, 8: 128.0}       # read 8 values + write 8 values per cell-update
 SMS, FP32_LANES = 152, 128                 # GB300: SMs, FP32 lanes per SM
 E2E_CHUNKS = 32                            # chunks of the host-streamed end-to-end leg
+OOC_BUDGET = 4 << 30                       # device budget of the out-of-core leg, FP32 (bytes; x2 for FP64)
 # DRAM bytes (read + write) per cell-update of the fused step kernel, FP32, 32^3 patches,
 # per tile configuration (the two the autotuner picks between on this machine):
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a 192^3 box of the
@@ -237,6 +241,49 @@ def _time_ms(stream, fn, n):
     return e0.elapsed_time(e1) / n
 
 
+def split_leg(args, b, host, geom, ws, rank, local, cfg):
+    """N > 1: the box repeated N times along z (512 x 512 x 512N for the default workload)
+    split into one slab of patch layers per GPU (domain.SlabDomain): per step each rank
+    sends its bottom and top patch layers to its neighbours (NCCL send/recv, into the
+    receiver's memory), fills its guard zones, takes its CFL dt, joins the minimum over
+    ranks (all_reduce) and updates its patches.  Each rank holds the state of the N = 1 box
+    (the field is periodic, so the repeated box is continuous), so per-GPU work stays that
+    of N = 1.  Returns (ms of args.steps steps on this rank, launches, clock sampler)."""
+    from paper_2508_09568_gb300 import workloads as W
+    from paper_2508_09568_gb300.domain import SlabDomain, step_distributed
+    nl = int(geom.domain[2] // geom.patch_n[0][2])
+    gg = W.uniform_geometry([int(geom.domain[0]), int(geom.domain[1]), int(geom.domain[2]) * ws],
+                            [int(v) for v in geom.patch_n[0]], dx=geom.dx)
+    dom = SlabDomain(gg, rank * nl, (rank + 1) * nl, dtype=b.dtype, gamma=b._params["gamma"],
+                     courant=b._params["courant"], device=str(b.device))
+    dom.b.set_mode(2, cfg)
+    with torch.cuda.stream(dom.b.stream):
+        dom.b.current().zero_()
+        dom.b.current()[:host.numel()].copy_(host, non_blocking=True)
+    dom.b.stream.synchronize()
+    for _ in range(args.warmup):
+        step_distributed(dom, rank, ws)
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = dom.b.launch_count()
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(cur)
+        for _ in range(args.steps):
+            step_distributed(dom, rank, ws)
+        cur.wait_stream(dom.b.stream)
+        e1.record(cur)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = dom.b.launch_count() - l0
+    code, msg = dom.b.error()
+    dom.close()
+    if code != 0:
+        raise RuntimeError(f"device error in the split-domain steps: {msg}")
+    return e0.elapsed_time(e1), launches, clk
+
+
 def ragged_leg(dev, steps):
     """The ragged box: 1566 patches of 16^3 / 24^3 / 32^3 (24.55 M cells), FP32, the step in a
     CUDA graph with one persistent launch per tile configuration, configurations chosen per
@@ -357,14 +404,43 @@ def e2e_leg(b, host, host_int, cells, ws, ke):
     tp = timed(lambda k: b.advance_streamed(host, k, E2E_CHUNKS), ke)
     ks = 2
     ts = timed(lambda k: [b.advance_host(host, 1) for _ in range(k)], ks)
+    ooc = out_of_core_leg(b, host_int, cells, ws, max(2, min(ke, 6)))
     return {"value": cells * ke * ws / te, "unit": UNIT, "h2d_bytes_per_step": ibytes,
-            "d2h_bytes_per_step": ibytes, "steps": ke,
+            "d2h_bytes_per_step": ibytes, "steps": ke, "out_of_core": ooc,
             "path": f"mhd_bunch_advance_streamed_interior, at most {E2E_CHUNKS} chunks cut at whole waves of "
                     "the update, pinned host state (owned cells only; ghost cells rebuilt on the device)",
             "state_layout": {"value": cells * ke * ws / tp, "steps": ke, "h2d_bytes_per_step": b.nbytes,
                              "path": f"mhd_bunch_advance_streamed, {E2E_CHUNKS} chunks (ghost cells included)"},
             "serial": {"value": cells * ks * ws / ts, "steps": ks,
                        "path": "mhd_bunch_advance_host one step per call: H2D, fill, dt, step, D2H"}}
+
+
+def out_of_core_leg(b, host_int, cells, ws, k):
+    """The box stepped with a device working set capped below its own size
+    (mhd_bunch_advance_out_of_core on a handle that holds no device state): the interior
+    state and a scratch buffer of the same size in pinned host memory, z-layers of patches
+    streamed through a ring on the device, a CFL pass and an update pass per step."""
+    from paper_2508_09568_gb300.bunch import MHDBunch
+    h = MHDBunch(b.geom, dtype=b.dtype, gamma=b._params["gamma"], courant=b._params["courant"],
+                 device=str(b.device), bind=False)
+    state = host_int.clone().pin_memory()
+    scratch = torch.empty_like(state).pin_memory()
+    ibytes = h.interior_size()[0]
+    budget = OOC_BUDGET * (b.rb // 4)
+    h.advance_out_of_core(state, scratch, 1, budget)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    h.advance_out_of_core(state, scratch, k, budget)
+    t = allmax(time.perf_counter() - t0, ws)
+    h.close()
+    nl = int(b.geom.domain[2] // b.geom.patch_n[0][2])
+    return {"value": cells * k * ws / t, "unit": UNIT, "steps": k, "device_budget_bytes": budget,
+            "state_bytes": b.nbytes, "host_interior_bytes": ibytes,
+            "h2d_bytes_per_step": 2 * ibytes * (nl + 2) // nl, "d2h_bytes_per_step": ibytes,
+            "path": "mhd_bunch_advance_out_of_core: working set capped at device_budget_bytes (below the size of "
+                    "one state buffer and of the host state), per step a CFL pass and an update pass over "
+                    "z-layers of patches"}
 
 
 def adjoint_leg(dev, dtype, rollout_steps=200, ckpt=10, reps=5):
@@ -456,7 +532,9 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps,
             "warmup": warm, "ms_per_step": 1e3 * tot / max(steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args, geom.npatch), "sample": sample_txt},
+            "config": {"workload": workload_name(args, geom.npatch) if ws == 1 else
+                      f"the {workload_name(args, geom.npatch)} repeated {ws} times along z, split into one slab of "
+                      f"{int(geom.domain[2] // geom.patch_n[0][2])} patch layers per GPU", "sample": sample_txt},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": sample_txt},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -518,25 +596,28 @@ def run_ours(args, ws, rank, local):
         cfg = b.autotune(None)
     tile = b.config_info(cfg)
 
-    # ---- timed region: graph replay of (fill -> CFL dt -> step), K steps
-    dts = torch.zeros(1, dtype=torch.float64, device=dev)
-    b.graph_capture(1, dts)
-    for _ in range(args.warmup):
-        b.graph_launch()
-    b.stream.synchronize()
-    l0 = b.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(ws)
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        e0.record(b.stream)
-        for _ in range(args.steps):
+    if ws == 1:
+        # ---- timed region: graph replay of (fill -> CFL dt -> step), K steps
+        dts = torch.zeros(1, dtype=torch.float64, device=dev)
+        b.graph_capture(1, dts)
+        for _ in range(args.warmup):
             b.graph_launch()
-        e1.record(b.stream)
+        b.stream.synchronize()
+        l0 = b.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
         torch.cuda.synchronize()
-    barrier(ws)
-    launches = b.launch_count() - l0
-    ms = e0.elapsed_time(e1)
+        with Clocks(local) as clk:
+            e0.record(b.stream)
+            for _ in range(args.steps):
+                b.graph_launch()
+            e1.record(b.stream)
+            torch.cuda.synchronize()
+        barrier(ws)
+        launches = b.launch_count() - l0
+        ms = e0.elapsed_time(e1)
+    else:
+        ms, launches, clk = split_leg(args, b, host, geom, ws, rank, local, cfg)
     ms_max = allmax(ms, ws)
     value = cells * args.steps * ws / (ms_max * 1e-3)
     clocks = clk.summary()
@@ -626,11 +707,15 @@ def run_ours(args, ws, rank, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": {"workload": workload_name(args, geom.npatch),
+           "config": {"workload": workload_name(args, geom.npatch) if ws == 1 else
+                      f"the {workload_name(args, geom.npatch)} repeated {ws} times along z, split into one slab of "
+                      f"{int(geom.domain[2] // geom.patch_n[0][2])} patch layers per GPU",
                       "cells": cells, "patches": geom.npatch, "patch": args.patch,
                       "tile": {"x": tile[0], "y": tile[1], "threads": tile[2]},
                       "l2": f"inputs larger than L2 (state {b.nbytes / 1e9:.2f} GB per buffer)",
-                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+                      "parallelism": "single GPU" if ws == 1 else
+                      f"z-slab split over {ws} GPUs: per step one patch layer sent each way per rank (NCCL "
+                      "send/recv) and an allreduce-min of dt; value counts the cells of all slabs"},
            "roofline": roof, "hbm_roofline": hbm_roof,
            "kernels_ms": {"fill_cfl": t_fc, "step": t_step, "fill_guards_alone": t_fill, "cfl_dt_alone": t_cfl,
                           "step_hll_flux": t_step_hll},

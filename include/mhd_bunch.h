@@ -260,6 +260,38 @@ int mhd_bunch_interior_size(const mhd_bunch *b, size_t *bytes, int64_t *patch_of
 int mhd_bunch_advance_streamed_interior(mhd_bunch *b, void *host_interior, int nsteps, int nchunks,
                                         double *t_out);
 
+/* ---------------------------------------------------------------------------------------
+ * Slabs of a z-layer decomposition of the box (one handle per GPU of a domain split over
+ * several GPUs; patches are independent given their guard zones, Secs. 2.2 and 4).
+ *
+ * mhd_bunch_set_slab, called once after mhd_bunch_set_geometry (the whole box: equal
+ * patches on a grid, x fastest, then y, then z, 3D), makes the handle own the patch layers
+ * z0 <= layer < z1 only.  Its state (mhd_bunch_state_size, to be bound again with
+ * mhd_bunch_bind) then holds the L = z1 - z0 owned layers in slots 0..L-1 and two halo
+ * layers: slot L the layer below z0, slot L+1 the layer above z1-1 (periodic wrap across
+ * the box; across an outflow box face the halo is never read).  Guard fill, CFL dt, steps,
+ * graphs, modes and the autotuner act on the owned patches, reading the halo slots where
+ * the guard zones reach the neighbouring layers; the streamed, out-of-core and
+ * asynchronous advances and the adjoint are not available (MHD_EINVAL).  Patch p of the
+ * handle is owned patch p (layer z0 + p / patches_per_layer), mhd_bunch_interior_size and
+ * the interior layout refer to the owned patches.
+ *
+ * Per step the caller exchanges halos: mhd_bunch_slab_pack copies the interiors of the
+ * bottom and top owned layers of the current state into `bottom` / `top` (device buffers
+ * of layer_bytes, interior layout of one layer's patches in order; either may be NULL);
+ * the neighbours' copies arrive through the caller's transport (NCCL, peer copies, ...)
+ * and mhd_bunch_slab_unpack writes them into the halo slots of the current state (below:
+ * the top layer of the slab underneath, above: the bottom layer of the slab on top; either
+ * may be NULL).  Then guard fill + dt on the slab, the minimum dt over all slabs, and the
+ * step.  Stream-ordered on the bound stream.  MHD_ESTATE before set_geometry, on a handle
+ * that is a slab already (set_slab) or is not one (info, pack, unpack); MHD_EINVAL for other
+ * geometries or layer ranges. */
+int mhd_bunch_set_slab(mhd_bunch *b, int z0, int z1);
+int mhd_bunch_slab_info(const mhd_bunch *b, int *layers, int64_t *patches_per_layer,
+                        size_t *layer_bytes);
+int mhd_bunch_slab_pack(mhd_bunch *b, void *bottom, void *top);
+int mhd_bunch_slab_unpack(mhd_bunch *b, const void *below, const void *above);
+
 /* Host-resident state larger than the device memory this call may use (the paper's
  * bunches staged from the host every update, Secs. 2.4 and 4, for a domain that does not
  * fit in HBM).  host_state holds the state in the interior layout (mhd_bunch_interior_size

@@ -44,10 +44,13 @@ class MHDBunch:
     riemann  face-flux solver: capi.MHD_RIEMANN_HLLD (default) or capi.MHD_RIEMANN_HLL
     bind     allocate and bind the two device state buffers (False: the handle holds no
              state on the device; only advance_out_of_core, which streams host state, runs)
+    slab     (z0, z1): own only the patch layers z0 <= layer < z1 of the box plus two halo
+             layers (mhd_bunch_set_slab; domain.SlabDomain drives it)
     """
 
     def __init__(self, geom: Geometry, dtype=torch.float32, gamma=5.0 / 3.0, courant=0.8, limiter=0,
-                 device="cuda:0", stream: torch.cuda.Stream | None = None, riemann: int = 0, bind: bool = True):
+                 device="cuda:0", stream: torch.cuda.Stream | None = None, riemann: int = 0, bind: bool = True,
+                 slab: tuple | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("MHDBunch needs a CUDA device (no CPU fallback)")
         self.lib = capi.load()
@@ -74,10 +77,13 @@ class MHDBunch:
                                                        dom.ctypes.data_as(capi.I64P), bc.ctypes.data_as(capi.I32P)))
             capi.check(self.lib.mhd_bunch_set_params(h, float(gamma), float(courant), int(limiter)))
             capi.check(self.lib.mhd_bunch_set_riemann(h, int(riemann)))
+            self.slab = None if slab is None else (int(slab[0]), int(slab[1]))
+            if self.slab is not None:
+                capi.check(self.lib.mhd_bunch_set_slab(h, self.slab[0], self.slab[1]))
             nbytes = ct.c_size_t()
             offs = np.zeros(geom.npatch, dtype=np.int64)
             capi.check(self.lib.mhd_bunch_state_size(h, ct.byref(nbytes), offs.ctypes.data_as(capi.I64P)))
-            if not np.array_equal(offs, geom.offsets()):
+            if self.slab is None and not np.array_equal(offs, geom.offsets()):
                 raise RuntimeError("library state layout differs from the workload layout")
             self.nbytes = nbytes.value
             n = self.nbytes // self.rb
@@ -266,6 +272,22 @@ class MHDBunch:
         n = ct.c_int64()
         capi.check(self.lib.mhd_bunch_launch_count(self.h, ct.byref(n)))
         return n.value
+
+    def slab_info(self):
+        """(owned layers, patches per layer, bytes of one layer in the interior layout)."""
+        nl, ppl, lb = ct.c_int(), ct.c_int64(), ct.c_size_t()
+        capi.check(self.lib.mhd_bunch_slab_info(self.h, ct.byref(nl), ct.byref(ppl), ct.byref(lb)))
+        return nl.value, ppl.value, lb.value
+
+    def slab_pack(self, bottom: torch.Tensor | None, top: torch.Tensor | None):
+        """Interiors of the bottom / top owned layers into device tensors (on the bunch stream)."""
+        capi.check(self.lib.mhd_bunch_slab_pack(self.h, None if bottom is None else ct.c_void_p(bottom.data_ptr()),
+                                                None if top is None else ct.c_void_p(top.data_ptr())))
+
+    def slab_unpack(self, below: torch.Tensor | None, above: torch.Tensor | None):
+        """The neighbours' layers into the halo slots (on the bunch stream)."""
+        capi.check(self.lib.mhd_bunch_slab_unpack(self.h, None if below is None else ct.c_void_p(below.data_ptr()),
+                                                  None if above is None else ct.c_void_p(above.data_ptr())))
 
     def twin(self) -> "MHDBunch":
         """A second handle on the same geometry and parameters with its own stream, state

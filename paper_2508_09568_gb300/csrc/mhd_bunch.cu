@@ -157,6 +157,15 @@ struct mhd_bunch {
         std::vector<int> first, count;       // per bunch
     };
     std::vector<BunchTiles> btiles;
+    // slab of a z-layer decomposition (mhd_bunch_set_slab): the handle owns layers
+    // [slab_z0, slab_z1) of the box's patch grid, stored in slots 0..L-1 of the state, and
+    // two halo layers (the layer below in slot L, the layer above in slot L+1) that the
+    // caller fills (mhd_bunch_slab_unpack) from its neighbours before each guard fill
+    bool slab = false;
+    int slab_z0 = 0, slab_z1 = 0, slab_nl = 0;
+    int64_t slab_ppl = 0;
+    PatchDev* d_slab_slots = nullptr;    // [(L+2) * ppl]: every patch slot, for the layer copies
+    int64_t* d_slab_ioff = nullptr;      // [ppl]: interior-layout offsets within one layer
     // captured step sequences; with an odd step count the second starts from the other buffer
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -350,6 +359,11 @@ StepHostArgs step_args(mhd_bunch* b, const double* dt_ptr, double dt_val) {
     a.riemann = b->riemann;
     a.err = b->d_err;
     return a;
+}
+
+int not_slab(const mhd_bunch* b) {
+    if (b->slab) return fail(MHD_EINVAL, "not available on a slab handle (mhd_bunch_set_slab)");
+    return MHD_OK;
 }
 
 int ready(const mhd_bunch* b) {
@@ -780,6 +794,7 @@ int mhd_bunch_create_ragged(const int32_t* patch_n, int npatch, int guard, int n
 int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patch_origin,
                            const int64_t domain_cells[3], const int32_t bc[6]) try {
     if (!b || !dx || !patch_origin || !domain_cells || !bc) return fail(MHD_EINVAL, "NULL argument");
+    if (b->slab) return fail(MHD_ESTATE, "the geometry of a slab handle is fixed");
     for (int d = 0; d < 3; ++d) {
         if (!(dx[d] > 0) || !std::isfinite(dx[d])) return fail(MHD_EINVAL, "dx must be positive");
         if (domain_cells[d] < 1 || domain_cells[d] > (1LL << 30)) return fail(MHD_EINVAL, "bad domain size");
@@ -873,6 +888,142 @@ int mhd_bunch_set_geometry(mhd_bunch* b, const double dx[3], const int64_t* patc
     int rc = build_tiles(b);
     if (rc != MHD_OK) return rc;
     b->have_geom = true;
+    return MHD_OK;
+} MHD_CATCH_ALL
+
+int mhd_bunch_set_slab(mhd_bunch* b, int z0, int z1) try {
+    if (!b) return fail(MHD_EINVAL, "handle is NULL");
+    if (!b->have_geom) return fail(MHD_ESTATE, "mhd_bunch_set_geometry has not been called");
+    if (b->slab) return fail(MHD_ESTATE, "the handle is a slab already");
+    if (b->ndim != 3) return fail(MHD_EINVAL, "slabs need a 3D box");
+    const int P = b->npatch;
+    const int nx = b->pn[0], ny = b->pn[1], nz = b->pn[2];
+    int64_t np3[3];
+    for (int d = 0; d < 3; ++d) np3[d] = b->domain[d] / b->pn[d];
+    const int64_t ppl = np3[0] * np3[1];
+    const int NL = (int)np3[2];
+    bool grid = ppl * NL == P && b->d_nboff != nullptr;
+    for (int p = 0; p < P && grid; ++p)
+        grid = b->pn[3 * p] == nx && b->pn[3 * p + 1] == ny && b->pn[3 * p + 2] == nz &&
+               b->origin[3 * p] == (p % np3[0]) * nx && b->origin[3 * p + 1] == ((p / np3[0]) % np3[1]) * ny &&
+               b->origin[3 * p + 2] == (p / ppl) * nz;
+    if (!grid) return fail(MHD_EINVAL, "slabs need equal patches on a grid, x fastest in patch order");
+    if (z0 < 0 || z1 > NL || z0 >= z1) return fail(MHD_EINVAL, "need 0 <= z0 < z1 <= number of patch layers");
+    const int L = z1 - z0;
+    const PatchDev h0 = b->hp[0];
+    const int64_t pe = 8LL * h0.X * h0.Y * h0.Z;
+    const bool per_lo = b->bc[4] == MHD_BC_PERIODIC, per_hi = b->bc[5] == MHD_BC_PERIODIC;
+    // slot of layer g (z-neighbour direction sz) as seen from an owned layer
+    auto slot_of = [&](int g, int sz, int gown) -> int {
+        if (g < 0 || g >= NL) {
+            if ((g < 0 && !per_lo) || (g >= NL && !per_hi)) return gown - z0;   // outflow: never read
+            g = (g + NL) % NL;
+        }
+        if (g >= z0 && g < z1) return g - z0;
+        return sz < 0 ? L : L + 1;
+    };
+    std::vector<PatchDev> hp;
+    std::vector<int64_t> offs, nb;
+    std::vector<int> pn;
+    std::vector<int64_t> origin;
+    for (int g = z0; g < z1; ++g)
+        for (int64_t j = 0; j < ppl; ++j) {
+            const int p = (int)(g * ppl + j);
+            PatchDev q = b->hp[p];
+            q.off = ((int64_t)(g - z0) * ppl + j) * pe;
+            hp.push_back(q);
+            offs.push_back(q.off);
+            for (int d = 0; d < 3; ++d) {
+                pn.push_back(b->pn[3 * p + d]);
+                origin.push_back(b->origin[3 * p + d]);
+            }
+            const int64_t ix = j % np3[0], iy = j / np3[0];
+            for (int sz = -1; sz <= 1; ++sz)
+                for (int sy = -1; sy <= 1; ++sy)
+                    for (int sx = -1; sx <= 1; ++sx) {
+                        const int64_t jx = ((ix + sx) % np3[0] + np3[0]) % np3[0];
+                        const int64_t jy = ((iy + sy) % np3[1] + np3[1]) % np3[1];
+                        nb.push_back(((int64_t)slot_of(g + sz, sz, g) * ppl + jy * np3[0] + jx) * pe);
+                    }
+        }
+    std::vector<PatchDev> slots((size_t)(L + 2) * ppl);
+    for (int sl = 0; sl < L + 2; ++sl)
+        for (int64_t j = 0; j < ppl; ++j) {
+            PatchDev q = h0;
+            q.off = ((int64_t)sl * ppl + j) * pe;
+            slots[(size_t)sl * ppl + j] = q;
+        }
+    std::vector<int64_t> ioff(ppl);
+    for (int64_t j = 0; j < ppl; ++j) ioff[j] = j * 8LL * nx * ny * nz;
+    release_graph(b);
+    free_tiles(b);
+    cudaFree(b->d_patches);
+    b->d_patches = nullptr;
+    cudaFree(b->d_nboff);
+    b->d_nboff = nullptr;
+    cudaFree(b->d_partial_fc);
+    b->d_partial_fc = nullptr;
+    b->npatch = L * (int)ppl;
+    b->hp = hp;
+    b->offs = offs;
+    b->pn = pn;
+    b->origin = origin;
+    b->state_bytes = (size_t)(L + 2) * ppl * pe * b->rb;
+    b->buf[0] = b->buf[1] = nullptr;       // bind buffers of the slab's size
+    b->ioff_h.clear();
+    CK(cudaMalloc(&b->d_patches, sizeof(PatchDev) * hp.size()));
+    CK(cudaMemcpy(b->d_patches, hp.data(), sizeof(PatchDev) * hp.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&b->d_nboff, sizeof(int64_t) * nb.size()));
+    CK(cudaMemcpy(b->d_nboff, nb.data(), sizeof(int64_t) * nb.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&b->d_partial_fc, (size_t)b->npatch * h0.Z * b->rb));
+    CK(cudaMalloc(&b->d_slab_slots, sizeof(PatchDev) * slots.size()));
+    CK(cudaMemcpy(b->d_slab_slots, slots.data(), sizeof(PatchDev) * slots.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&b->d_slab_ioff, sizeof(int64_t) * ppl));
+    CK(cudaMemcpy(b->d_slab_ioff, ioff.data(), sizeof(int64_t) * ppl, cudaMemcpyHostToDevice));
+    b->slab = true;
+    b->slab_z0 = z0;
+    b->slab_z1 = z1;
+    b->slab_nl = NL;
+    b->slab_ppl = ppl;
+    return build_tiles(b);
+} MHD_CATCH_ALL
+
+int mhd_bunch_slab_info(const mhd_bunch* b, int* layers, int64_t* patches_per_layer, size_t* layer_bytes) try {
+    if (!b || !layers || !patches_per_layer || !layer_bytes) return fail(MHD_EINVAL, "NULL argument");
+    if (!b->slab) return fail(MHD_ESTATE, "not a slab handle");
+    *layers = b->slab_z1 - b->slab_z0;
+    *patches_per_layer = b->slab_ppl;
+    *layer_bytes = (size_t)b->slab_ppl * 8 * b->pn[0] * b->pn[1] * b->pn[2] * b->rb;
+    return MHD_OK;
+} MHD_CATCH_ALL
+
+// interior of layer slot sl of the current state <-> a buffer in the interior layout
+int slab_copy(mhd_bunch* b, int sl, void* buf, int to_padded) {
+    const int nz = b->pn[2];
+    interior_copy_kernel<<<dim3(nz, (unsigned)b->slab_ppl), 256, 0, b->stream>>>(
+        static_cast<unsigned*>(b->buf[b->cur]), static_cast<unsigned*>(buf), b->d_slab_slots + (size_t)sl * b->slab_ppl,
+        b->d_slab_ioff, 0, (int)b->slab_ppl, b->rb / 4, to_padded);
+    ++b->launches;
+    CK(cudaGetLastError());
+    return MHD_OK;
+}
+
+int mhd_bunch_slab_pack(mhd_bunch* b, void* bottom, void* top) try {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!b->slab) return fail(MHD_ESTATE, "not a slab handle");
+    if (bottom && (rc = slab_copy(b, 0, bottom, 0))) return rc;
+    if (top && (rc = slab_copy(b, b->slab_z1 - b->slab_z0 - 1, top, 0))) return rc;
+    return MHD_OK;
+} MHD_CATCH_ALL
+
+int mhd_bunch_slab_unpack(mhd_bunch* b, const void* below, const void* above) try {
+    int rc = ready(b);
+    if (rc) return rc;
+    if (!b->slab) return fail(MHD_ESTATE, "not a slab handle");
+    const int L = b->slab_z1 - b->slab_z0;
+    if (below && (rc = slab_copy(b, L, const_cast<void*>(below), 1))) return rc;
+    if (above && (rc = slab_copy(b, L + 1, const_cast<void*>(above), 1))) return rc;
     return MHD_OK;
 } MHD_CATCH_ALL
 
@@ -1207,6 +1358,7 @@ int mhd_bunch_graph_launch(mhd_bunch* b) try {
 } MHD_CATCH_ALL
 
 int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t_out) try {
+    if (b && b->slab) return not_slab(b);
     int rc = ready(b);
     if (rc) return rc;
     if (!host_state || nsteps < 0) return fail(MHD_EINVAL, "bad argument");
@@ -1233,6 +1385,7 @@ int mhd_bunch_advance_host(mhd_bunch* b, void* host_state, int nsteps, double* t
 } MHD_CATCH_ALL
 
 int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int nchunks, double* t_out) try {
+    if (b && b->slab) return not_slab(b);
     int rc = ready(b);
     if (rc) return rc;
     if (!host_state || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1301,6 +1454,7 @@ int mhd_bunch_advance_streamed(mhd_bunch* b, void* host_state, int nsteps, int n
 
 int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int nsteps, int nchunks,
                                         double* t_out) try {
+    if (b && b->slab) return not_slab(b);
     int rc = ready(b);
     if (rc) return rc;
     if (!host_interior || nsteps < 1 || nchunks < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1400,6 +1554,7 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
                                   size_t device_budget, void* cuda_stream, double* t_out) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (!b->have_geom) return fail(MHD_ESTATE, "mhd_bunch_set_geometry has not been called");
+    if (b->slab) return not_slab(b);
     if (!host_state || !host_scratch || host_state == host_scratch || nsteps < 1 || device_budget == 0)
         return fail(MHD_EINVAL, "bad argument");
     if (b->ndim != 3) return fail(MHD_EINVAL, "the out-of-core advance needs a 3D box");
@@ -1646,6 +1801,7 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
 } MHD_CATCH_ALL
 
 int mhd_bunch_advance_async(mhd_bunch* b, double t_span, int max_rounds, int* rounds, int64_t* patch_updates) try {
+    if (b && b->slab) return not_slab(b);
     int rc = ready(b);
     if (rc) return rc;
     if (!(t_span >= 0) || !std::isfinite(t_span) || max_rounds < 1) return fail(MHD_EINVAL, "bad argument");
@@ -1835,6 +1991,8 @@ void mhd_bunch_destroy(mhd_bunch* b) {
     cudaFree(b->d_owner);
     cudaFree(b->d_nboff);
     cudaFree(b->d_partial_fc);
+    cudaFree(b->d_slab_slots);
+    cudaFree(b->d_slab_ioff);
     cudaFree(b->d_work);
     cudaFree(b->d_partial);
     cudaFree(b->d_counter);
@@ -1852,6 +2010,7 @@ const char* mhd_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 
 extern "C" int mhd_bunch_step_adjoint(mhd_bunch* b, double dt, const void* U_n, const void* lam_next, void* lam) try {
+    if (b && b->slab) return not_slab(b);
     int rc = ready(b);
     if (rc) return rc;
     if (!U_n || !lam_next || !lam) return fail(MHD_EINVAL, "NULL argument");
