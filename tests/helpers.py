@@ -15,7 +15,8 @@ TOL_STEP = {torch.float64: 1e-12, torch.float32: 1e-5}
 # the scale; 1e-4 leaves a margin of about 10 and still fails a single cell that is off by
 # 0.01 % of the scale, far below what a wrong face, edge or ragged-tail cell would give.
 # FP64: the same argument with 2^-53 gives ~1e-13; 1e-10 is the same margin as the L1
-# bound of multi-step runs.
+# bound of multi-step runs.  Observed per step on a GB300 (Sod, Orszag-Tang 64^2, 3D boxes
+# with ragged tiles): FP32 at most 1.4e-7, FP64 at most 3.6e-16.
 TOL_MAX = {torch.float64: 1e-10, torch.float32: 1e-4}
 
 
