@@ -285,7 +285,7 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch *b, void *host_interior, int n
  * may be NULL).  Then guard fill + dt on the slab, the minimum dt over all slabs, and the
  * step.  Stream-ordered on the bound stream.  MHD_ESTATE before set_geometry, on a handle
  * that is a slab already (set_slab) or is not one (info, pack, unpack); MHD_EINVAL for other
- * geometries or layer ranges. */
+ * geometries (or more than 65535 patches per z-layer) or layer ranges. */
 int mhd_bunch_set_slab(mhd_bunch *b, int z0, int z1);
 int mhd_bunch_slab_info(const mhd_bunch *b, int *layers, int64_t *patches_per_layer,
                         size_t *layer_bytes);
@@ -312,8 +312,8 @@ int mhd_bunch_slab_unpack(mhd_bunch *b, const void *below, const void *above);
  * the device-resident steps (mhd_bunch_fill_cfl_device + mhd_bunch_step_device_dt)
  * bitwise.  Runs on cuda_stream (NULL: legacy default stream) and the library's copy
  * streams and synchronises them; returns the device error word as mhd_bunch_get_error
- * would.  MHD_EINVAL for other geometries or bad arguments, MHD_ESTATE before
- * set_geometry. */
+ * would.  MHD_EINVAL for other geometries (or more than 65535 patches per z-layer) or bad
+ * arguments, MHD_ESTATE before set_geometry. */
 int mhd_bunch_advance_out_of_core(mhd_bunch *b, void *host_state, void *host_scratch, int nsteps,
                                   size_t device_budget, void *cuda_stream, double *t_out);
 

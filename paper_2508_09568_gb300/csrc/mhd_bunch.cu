@@ -908,6 +908,7 @@ int mhd_bunch_set_slab(mhd_bunch* b, int z0, int z1) try {
                b->origin[3 * p] == (p % np3[0]) * nx && b->origin[3 * p + 1] == ((p / np3[0]) % np3[1]) * ny &&
                b->origin[3 * p + 2] == (p / ppl) * nz;
     if (!grid) return fail(MHD_EINVAL, "slabs need equal patches on a grid, x fastest in patch order");
+    if (ppl > 65535) return fail(MHD_EINVAL, "more than 65535 patches per z-layer");
     if (z0 < 0 || z1 > NL || z0 >= z1) return fail(MHD_EINVAL, "need 0 <= z0 < z1 <= number of patch layers");
     const int L = z1 - z0;
     const PatchDev h0 = b->hp[0];
@@ -1572,6 +1573,7 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
                b->origin[3 * p + 2] == (p / ppl) * nz;
     }
     if (!grid) return fail(MHD_EINVAL, "the out-of-core advance needs equal patches on a grid, x fastest in patch order");
+    if (ppl > 65535) return fail(MHD_EINVAL, "more than 65535 patches per z-layer");
     const PatchDev& h0 = b->hp[0];
     const int64_t pe = 8LL * h0.X * h0.Y * h0.Z;           // elements of a padded patch
     const int64_t ie = 8LL * nx * ny * nz;                 // elements of a patch's interior
