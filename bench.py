@@ -435,11 +435,11 @@ def out_of_core_leg(b, host_int, cells, ws, k):
     t0 = time.perf_counter()
     h.advance_out_of_core(state, scratch, k, budget)
     t = allmax(time.perf_counter() - t0, ws)
+    up, down = h.io_bytes
     h.close()
-    nl = int(b.geom.domain[2] // b.geom.patch_n[0][2])
     return {"value": cells * k * ws / t, "unit": UNIT, "steps": k, "device_budget_bytes": budget,
             "state_bytes": b.nbytes, "host_interior_bytes": ibytes,
-            "h2d_bytes_per_step": 2 * ibytes * (nl + 2) // nl, "d2h_bytes_per_step": ibytes,
+            "h2d_bytes_per_step": up // k, "d2h_bytes_per_step": down // k,
             "path": "mhd_bunch_advance_out_of_core: working set capped at device_budget_bytes (below the size of "
                     "one state buffer and of the host state), per step a CFL pass and an update pass over "
                     "z-layers of patches"}

@@ -307,15 +307,18 @@ int mhd_bunch_slab_unpack(mhd_bunch *b, const void *below, const void *above);
  * with L the largest chunk of layers that fits (MHD_ENOMEM if one layer does not).  Per
  * step, two passes over the chunks, each window of layers uploaded once per pass, its
  * layers above and below included: (1) guard fill + CFL rates of every chunk, dt = the
- * smallest chunk dt, i.e. the global CFL dt; (2) guard fill and update of each chunk,
- * its new interior copied back into the other host buffer.  The results equal those of
+ * smallest chunk dt, i.e. the global CFL dt; (2) guard fill and update of each chunk, in
+ * reverse order (the last chunk's window is still on the device), its new interior copied
+ * back into the other host buffer.  The results equal those of
  * the device-resident steps (mhd_bunch_fill_cfl_device + mhd_bunch_step_device_dt)
  * bitwise.  Runs on cuda_stream (NULL: legacy default stream) and the library's copy
  * streams and synchronises them; returns the device error word as mhd_bunch_get_error
- * would.  MHD_EINVAL for other geometries (or more than 65535 patches per z-layer) or bad
+ * would.  io_bytes (may be NULL) receives the bytes copied host -> device and device ->
+ * host over the call.  MHD_EINVAL for other geometries (or more than 65535 patches per z-layer) or bad
  * arguments, MHD_ESTATE before set_geometry. */
 int mhd_bunch_advance_out_of_core(mhd_bunch *b, void *host_state, void *host_scratch, int nsteps,
-                                  size_t device_budget, void *cuda_stream, double *t_out);
+                                  size_t device_budget, void *cuda_stream, double *t_out,
+                                  size_t io_bytes[2]);
 
 /* Adjoint of one step at fixed dt (the reverse of mhd_bunch_step, including the guard
  * fill): given U^n (interior valid; ghosts are re-filled internally) and the cotangent

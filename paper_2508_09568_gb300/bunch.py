@@ -224,15 +224,18 @@ class MHDBunch:
         """nsteps steps of a host-resident state in the interior layout (pinned CPU tensors;
         host_scratch of the same size is overwritten) using at most device_budget bytes of
         device memory for the working set (mhd_bunch_advance_out_of_core); the new state is
-        in host_state; returns the simulated time."""
+        in host_state; returns the simulated time.  self.io_bytes: (host -> device,
+        device -> host) bytes of the call."""
         nb = self.interior_size()[0]
         _check_buffer(host_state, self.dtype, nb, False, "host_state")
         _check_buffer(host_scratch, self.dtype, nb, False, "host_scratch")
         t = ct.c_double()
+        io = (ct.c_size_t * 2)()
         capi.check(self.lib.mhd_bunch_advance_out_of_core(self.h, ct.c_void_p(host_state.data_ptr()),
                                                           ct.c_void_p(host_scratch.data_ptr()), int(nsteps),
                                                           ct.c_size_t(int(device_budget)),
-                                                          ct.c_void_p(self.stream.cuda_stream), ct.byref(t)))
+                                                          ct.c_void_p(self.stream.cuda_stream), ct.byref(t), io))
+        self.io_bytes = (io[0], io[1])
         return t.value
 
     def advance_async(self, t_span: float, max_rounds: int = 100000):

@@ -60,7 +60,7 @@ SIGNATURES = {
     "mhd_bunch_slab_info": (I, [P, ct.POINTER(I), I64P, ct.POINTER(ct.c_size_t)]),
     "mhd_bunch_slab_pack": (I, [P, P, P]),
     "mhd_bunch_slab_unpack": (I, [P, P, P]),
-    "mhd_bunch_advance_out_of_core": (I, [P, P, P, I, ct.c_size_t, P, DP]),
+    "mhd_bunch_advance_out_of_core": (I, [P, P, P, I, ct.c_size_t, P, DP, ct.POINTER(ct.c_size_t)]),
     "mhd_bunch_advance_async": (I, [P, D, I, ct.POINTER(I), I64P]),
     "mhd_bunch_async_round": (I, [P, I, I32P, DP, I, ct.POINTER(I)]),
     "mhd_bunch_step_adjoint": (I, [P, D, P, P, P]),

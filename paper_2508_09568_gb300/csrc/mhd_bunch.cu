@@ -1552,7 +1552,7 @@ int mhd_bunch_advance_streamed_interior(mhd_bunch* b, void* host_interior, int n
 } MHD_CATCH_ALL
 
 int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scratch, int nsteps,
-                                  size_t device_budget, void* cuda_stream, double* t_out) try {
+                                  size_t device_budget, void* cuda_stream, double* t_out, size_t* io_bytes) try {
     if (!b) return fail(MHD_EINVAL, "handle is NULL");
     if (!b->have_geom) return fail(MHD_ESTATE, "mhd_bunch_set_geometry has not been called");
     if (b->slab) return not_slab(b);
@@ -1741,6 +1741,16 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
         }
         return MHD_OK;
     };
+    // the same going down: chunk c after chunk c+1, whose window holds c's top two layers
+    auto load_window_down = [&](const char* hsrc, int c) -> int {
+        const int z0 = c * L, z1 = std::min(NL, z0 + L);
+        for (int g = z0 - 1; g <= z1 - 2; ++g) {
+            if ((g < 0 && !zper_lo) || (g >= NL && !zper_hi)) continue;
+            const int e = upload(hsrc, g);
+            if (e) return e;
+        }
+        return MHD_OK;
+    };
     for (int s = 0; s < nsteps; ++s) {
         const char* R = hbuf[r];
         char* W = hbuf[1 - r];
@@ -1756,11 +1766,16 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
         min_dt_kernel<<<1, 32, 0, st>>>(d_cdt, K, d_dts + s);
         ++b->launches;
         CK(cudaGetLastError());
-        // pass 2: guard fill, update, gather and download of every chunk
-        for (int c = 0; c < K; ++c) {
-            if ((rc = load_window(R, c))) return rc;
-            CK(b->K->fill(ring, d_ctab + cfirst[c], cnp[c], b->fg, d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->d_err, st));
-            ++b->launches;
+        // pass 2: guard fill, update, gather and download of every chunk, last chunk first:
+        // pass 1 left the last chunk's window in the ring with its guard zones filled, and
+        // going down each window shares its two top layers with the one before
+        for (int c = K - 1; c >= 0; --c) {
+            if (c < K - 1) {
+                if ((rc = load_window_down(R, c))) return rc;
+                CK(b->K->fill(ring, d_ctab + cfirst[c], cnp[c], b->fg, d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->d_err,
+                              st));
+                ++b->launches;
+            }
             StepHostArgs a = step_args(b, d_dts + s, 0.0);
             a.U = ring;
             a.Unew = ring_new;
@@ -1799,6 +1814,10 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
     rc = read_error(b, &code, nullptr, 0);
     if (rc) return rc;
     if (t_out) *t_out = std::accumulate(dts.begin(), dts.end(), 0.0);
+    if (io_bytes) {
+        io_bytes[0] = (size_t)nup * IL;
+        io_bytes[1] = (size_t)nsteps * P * ie * b->rb;
+    }
     return code;
 } MHD_CATCH_ALL
 

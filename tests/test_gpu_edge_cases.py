@@ -66,3 +66,25 @@ def test_uniform_state_is_stationary(dtype):
     assert abs(dt - 0.8 / rate) <= tol * dt
     got = interior_global(gpu_steps(b, [dt, dt]), geom)
     assert np.array_equal(got, interior_global(flat, geom))
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
+@pytest.mark.parametrize("shape", [(4096, 8, 8), (8, 8, 4096)], ids=["x4096", "z4096"])
+def test_largest_patch_extent(dtype, shape):
+    """The largest patch extent the library accepts (4096 cells) along x (128 tiles of 32 in
+    a row, 64-bit offsets across a 4,102-cell row) and along z (a tile marching 4,096
+    planes): one periodic patch, one step against the oracle.  On the 4096 x 8 x 8 patch the
+    seeded B_z is about 1e-3 of |B|, so the face field's relative L1 is taken as a vector
+    (R21)."""
+    geom, U, meta = W.small_box(ncell=shape, patch=shape, seed=43)
+    assert geom.npatch == 1
+    flat = rounded(W.to_patches(U, geom), dtype)
+    b = gpu_bunch(geom, flat, meta["gamma"], dtype)
+    b.fill_guards()
+    dt = b.cfl_dt()
+    b.step(dt)
+    got = interior_global(b.download(), geom)
+    ref = interior_global(oracle_steps(geom, flat, meta["gamma"], [dt], dtype=dtype), geom)
+    assert_parity(got, ref, dtype, b_vector=True)
+    code, msg = b.error()
+    assert code == 0, msg

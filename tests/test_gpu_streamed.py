@@ -131,6 +131,13 @@ def test_out_of_core_equals_device_resident(dtype, bcz):
         assert t == t_ref, budget
         got = W.from_interior(host.numpy().astype(np.float64), geom)
         assert np.array_equal(got, want), budget
+        # every step downloads the state once; with the whole box on the device (one
+        # chunk) it uploads the 16 layers and the two wrapped halos once (the update pass
+        # reuses the CFL pass's window)
+        assert ooc.io_bytes[1] == 3 * host_bytes
+        if budget == 1 << 34:
+            layers = 16 + (2 if bcz == "periodic" else 0)
+            assert ooc.io_bytes[0] == 3 * layers * host_bytes // 16
     ooc.close()
 
 
