@@ -19,7 +19,8 @@ static const StepLaunch kStepF32[] = {
 const PrecisionKernels& kernels_f32() {
     static const PrecisionKernels k{kStepF32, (int)(sizeof(kStepF32) / sizeof(kStepF32[0])), &launch_fill<float>,
                                     &launch_cfl<float>, &launch_adjoint<float>, AF_N,
-                                    &launch_fill_interp<float>, &launch_cfl_patch<float>, &launch_fill_cfl<float>};
+                                    &launch_fill_interp<float>, &launch_cfl_patch<float>, &launch_fill_cfl<float>,
+                                    &prepare_fill_cfl<float>};
     return k;
 }
 

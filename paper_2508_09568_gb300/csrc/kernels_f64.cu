@@ -13,7 +13,8 @@ static const StepLaunch kStepF64[] = {
 const PrecisionKernels& kernels_f64() {
     static const PrecisionKernels k{kStepF64, (int)(sizeof(kStepF64) / sizeof(kStepF64[0])), &launch_fill<double>,
                                     &launch_cfl<double>, &launch_adjoint<double>, AF_N,
-                                    &launch_fill_interp<double>, &launch_cfl_patch<double>, &launch_fill_cfl<double>};
+                                    &launch_fill_interp<double>, &launch_cfl_patch<double>, &launch_fill_cfl<double>,
+                                    &prepare_fill_cfl<double>};
     return k;
 }
 

@@ -76,12 +76,27 @@ static cudaError_t launch_fill(void* U, const PatchDev* patches, int npatch, con
 }
 
 template <typename R>
-static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, int npatch, const int64_t* nboff, int Zp,
-                                  double gamma, double courant, const double dxi[3], const int act[3], void* partial,
-                                  unsigned* counter, double* dt_out, unsigned* err, cudaStream_t s) {
-    fill_cfl_grid_kernel<R><<<(unsigned)npatch * (unsigned)Zp, 128, 0, s>>>(
-        static_cast<R*>(U), patches, nboff, Zp, gamma, courant, dxi[0], dxi[1], dxi[2], act[1], act[2],
-        static_cast<R*>(partial), counter, dt_out, err);
+static cudaError_t prepare_fill_cfl() {
+    return cudaFuncSetAttribute(fill_cfl_staged_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FILL_CFL_STAGED_MAX_SMEM);
+}
+
+// the staged pass where the plane fits its shared-memory cap, else the register version
+template <typename R>
+static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, const PatchDev& h0, int npatch,
+                                  const int64_t* nboff, int Zp, double gamma, double courant, const double dxi[3],
+                                  const int act[3], void* partial, unsigned* counter, double* dt_out, unsigned* err,
+                                  cudaStream_t s) {
+    const unsigned grid = (unsigned)npatch * (unsigned)Zp;
+    const size_t smem = fill_cfl_staged_smem<R>(h0.X, h0.Y, h0.nx, h0.ny, h0.gx, h0.gy);
+    if (fill_cfl_staged_fits<R>(h0))
+        fill_cfl_staged_kernel<R><<<grid, 256, smem, s>>>(static_cast<R*>(U), patches, nboff, Zp, gamma, courant,
+                                                          dxi[0], dxi[1], dxi[2], act[1], act[2],
+                                                          static_cast<R*>(partial), counter, dt_out, err);
+    else
+        fill_cfl_grid_kernel<R><<<grid, 128, 0, s>>>(static_cast<R*>(U), patches, nboff, Zp, gamma, courant, dxi[0],
+                                                     dxi[1], dxi[2], act[1], act[2], static_cast<R*>(partial),
+                                                     counter, dt_out, err);
     return cudaGetLastError();
 }
 

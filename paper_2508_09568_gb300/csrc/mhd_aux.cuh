@@ -428,6 +428,224 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
 }
 
 // ---------------------------------------------------------------------------------------
+// a1 + a2 fused and staged through shared memory, for regular grids whose plane fits (the
+// ghost values and the dt of fill_cfl_grid_kernel, bitwise).  One CTA per padded z-plane
+// of a patch puts every global load of its plane in flight at once: an interior plane
+// brings its own padded plane (8 contiguous blocks of X*Y reals, one per variable) into
+// shared memory with bulk copies (TMA) on an mbarrier, and the sources of its ghost cells,
+// the high x- and y-faces of its last column and row (the sources of the ghost cells
+// standing there) and the high z-faces (the next plane, or the neighbour above) with
+// element copies (cp.async); a z-ghost plane brings only its ghost sources.  The CTA then
+// waits for DRAM once, holding no registers for the data in flight, writes the ghost cells
+// and takes the rates from shared memory.  Only this CTA writes its plane's ghost cells,
+// and it does so after the copies have landed, so no copy reads a cell being written.
+// The wait on the bulk copies is bounded (one second of %globaltimer): past it the CTA
+// sets ERR_TIMEOUT, waits once more (bounded) for its copies, skips its work and reports
+// an infinite rate, so the launch still completes and the dt is not a valid one.
+// Dynamic shared memory, in elements: interior plane PL[8][X*Y] G[8][ng] FX[ny] FY[nx]
+// FZ[ny*nx] (ng = 2 gy X + 2 gx ny); z-ghost plane G[8][X*Y] (fill_cfl_staged_smem).
+// A plane whose address or byte size is not a multiple of 16 (no bulk copy) is brought in
+// with element copies of its interior cells instead.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__host__ __device__ inline size_t fill_cfl_staged_smem(int X, int Y, int nx, int ny, int gx, int gy) {
+    const size_t xy = (size_t)X * Y, ng = (size_t)2 * gy * X + (size_t)2 * gx * ny, nin = (size_t)nx * ny;
+    const size_t inner = 8 * xy + 8 * ng + ny + nx + nin, outer = 8 * xy;
+    return (inner > outer ? inner : outer) * sizeof(R);
+}
+// planes whose staging needs more than this take fill_cfl_grid_kernel (two CTAs per SM fit)
+constexpr size_t FILL_CFL_STAGED_MAX_SMEM = 113 * 1024;
+
+template <typename R>
+inline bool fill_cfl_staged_fits(const PatchDev& h0) {
+    return fill_cfl_staged_smem<R>(h0.X, h0.Y, h0.nx, h0.ny, h0.gx, h0.gy) <= FILL_CFL_STAGED_MAX_SMEM;
+}
+
+template <typename R>
+__device__ __forceinline__ void cp_async_elem_aux(R* smem_dst, const R* gsrc) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// phase 0 of the mbarrier at bar completed within limit_ns (false: gave up)
+__device__ __forceinline__ bool mbar_wait0(unsigned bar, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) fill_cfl_staged_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
+                                                             const int64_t* __restrict__ nboff, int Zp, double gamma_d,
+                                                             double courant, double dxi0_d, double dxi1_d,
+                                                             double dxi2_d, int act1, int act2, R* partial,
+                                                             unsigned* counter, double* dt_out, unsigned* err) {
+    extern __shared__ __align__(128) unsigned char fc_smem[];
+    __shared__ R red[32];
+    __shared__ bool last;
+    __shared__ __align__(8) uint64_t bar_mem;
+    const int p = blockIdx.x / Zp, z = blockIdx.x - p * Zp;
+    const PatchDev pt = patches[p];
+    const int64_t* nb = nboff + (int64_t)p * 27;
+    const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy, nx = pt.nx, ny = pt.ny;
+    const int XY = X * Y;
+    const int64_t vol = (int64_t)XY * pt.Z;
+    const int iz = z - pt.gz;
+    const bool zghost = iz < 0 || iz >= pt.nz;
+    const int nfull = zghost ? XY : 2 * gy * X;
+    const int ncnt = zghost ? XY : nfull + ny * 2 * gx;
+    const int nin = nx * ny;
+    R* plane = U + pt.off + (int64_t)z * XY;
+    R* PL = reinterpret_cast<R*>(fc_smem);
+    R* G = zghost ? PL : PL + 8 * XY;
+    R* FX = G + 8 * ncnt;
+    R* FY = FX + ny;
+    R* FZ = FY + nx;
+    const unsigned bar = static_cast<unsigned>(__cvta_generic_to_shared(&bar_mem));
+    // plane coordinates of the k-th ghost cell of the plane (the order of fill_grid_kernel)
+    auto coord = [&](int k, int& x, int& y) {
+        if (k < nfull) {
+            const int r = k / X;
+            x = k - r * X;
+            y = zghost ? r : (r < gy ? r : ny + r);
+        } else {
+            const int k2 = k - nfull;
+            const int r = k2 / (2 * gx), c = k2 - r * (2 * gx);
+            y = gy + r;
+            x = c < gx ? c : nx + c;
+        }
+    };
+    // 1. every load of the plane in flight
+    const bool bulk = !zghost && ((reinterpret_cast<uintptr_t>(plane) | ((size_t)XY * sizeof(R))) & 15) == 0;
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bytes = (unsigned)(XY * sizeof(R));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(8 * bytes)
+                         : "memory");
+#pragma unroll 1
+            for (int q = 0; q < 8; ++q) {
+                const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(PL + q * XY));
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
+                    "l"(plane + q * vol), "r"(bytes), "r"(bar)
+                    : "memory");
+            }
+        }
+    } else if (!zghost) {
+        for (int k = threadIdx.x; k < nin; k += blockDim.x) {
+            const int y = k / nx, x = k - y * nx;
+            const int c = (y + gy) * X + x + gx;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cp_async_elem_aux(PL + q * XY + c, plane + q * vol + c);
+        }
+    }
+    for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
+        int x, y;
+        coord(k, x, y);
+        const R* src = U + neighbour_source(pt, nb, x - gx, y - gy, iz);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cp_async_elem_aux(G + q * ncnt + k, src + q * vol);
+    }
+    if (!zghost) {
+        const bool top = iz + 1 == pt.nz;
+        if (act2)
+            for (int k = threadIdx.x; k < nin; k += blockDim.x) {
+                const int y = k / nx, x = k - y * nx;
+                cp_async_elem_aux(FZ + k, top ? U + 7 * vol + neighbour_source(pt, nb, x, y, pt.nz)
+                                              : plane + 7 * vol + (int64_t)XY + (int64_t)(y + gy) * X + x + gx);
+            }
+        for (int k = threadIdx.x; k < ny + nx; k += blockDim.x) {
+            if (k < ny) cp_async_elem_aux(FX + k, U + 5 * vol + neighbour_source(pt, nb, nx, k, iz));
+            else if (act1) cp_async_elem_aux(FY + (k - ny), U + 6 * vol + neighbour_source(pt, nb, k - ny, ny, iz));
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    bool ok = true;
+    if (bulk) ok = mbar_wait0(bar, 1000000000ull);
+    ok = __syncthreads_and(ok);
+    R vmax = R(0);
+    bool bad = false;
+    if (!ok) {
+        // copies that did not land in time: wait once more (bounded) so that none is still
+        // writing this CTA's shared memory when it exits, and report
+        mbar_wait0(bar, 1000000000ull);
+        if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+        vmax = R(INFINITY);
+    } else {
+        // 2. the ghost cells
+        for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
+            int x, y;
+            coord(k, x, y);
+            R* d = plane + (int64_t)y * X + x;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) d[q * vol] = G[q * ncnt + k];
+        }
+        // 3. the rates of the interior cells
+        if (!zghost) {
+            const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
+            const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
+            for (int k = threadIdx.x; k < nin; k += blockDim.x) {
+                const int y = k / nx, x = k - y * nx;
+                const int c = (y + gy) * X + x + gx;
+                R u[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) u[q] = PL[q * XY + c];
+                const R bxh = x + 1 < nx ? PL[5 * XY + c + 1] : FX[y];
+                const R byh = act1 ? (y + 1 < ny ? PL[6 * XY + c + X] : FY[x]) : R(0);
+                const R bzh = act2 ? FZ[k] : R(0);
+                const R rate = cell_rate_vals(u, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
+                if (!isfinite((double)rate)) bad = true;
+                else vmax = rate > vmax ? rate : vmax;
+            }
+        }
+    }
+    if (bad) atomicOr(err, ERR_PHYS);
+    const R bm = block_max(vmax, red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = bm;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        R v = R(0);
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+            const R w = ((volatile R*)partial)[k];
+            v = w > v ? w : v;
+        }
+        __syncthreads();
+        v = block_max(v, red);
+        if (threadIdx.x == 0) {
+            *dt_out = courant / (double)v;
+            *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Asynchronous stepping (patches at their own times, two time slices each: the current one
 // in buffer slice[p] of (U0, U1), the previous one in the other).
 // ---------------------------------------------------------------------------------------

@@ -280,6 +280,11 @@ int common_create(const int32_t* pn, int npatch, int guard, int nvar, int rb, mh
         delete b;
         return fail(MHD_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
+    e = b->K->prepare_fill_cfl();
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(MHD_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+    }
     for (int k : b->cfg_index) {
         e = b->K->step[k].prepare();
         if (e != cudaSuccess) {
@@ -441,8 +446,8 @@ int do_fill_cfl(mhd_bunch* b, double* dt_dev) {
         dxi[d] = 1.0 / b->dx[d];
         act[d] = active(b, d);
     }
-    CK(b->K->fill_cfl(b->buf[b->cur], b->d_patches, b->npatch, b->d_nboff, b->hp[0].Z, b->gamma, b->courant, dxi, act,
-                      b->d_partial_fc, b->d_counter, dt_dev, b->d_err, b->stream));
+    CK(b->K->fill_cfl(b->buf[b->cur], b->d_patches, b->hp[0], b->npatch, b->d_nboff, b->hp[0].Z, b->gamma, b->courant,
+                      dxi, act, b->d_partial_fc, b->d_counter, dt_dev, b->d_err, b->stream));
     b->launches++;
     return MHD_OK;
 }
@@ -1759,7 +1764,7 @@ int mhd_bunch_advance_out_of_core(mhd_bunch* b, void* host_state, void* host_scr
         // pass 1: guard fill + CFL rates of every chunk; dt = the smallest chunk dt
         for (int c = 0; c < K; ++c) {
             if ((rc = load_window(R, c))) return rc;
-            CK(b->K->fill_cfl(ring, d_ctab + cfirst[c], cnp[c], d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->gamma,
+            CK(b->K->fill_cfl(ring, d_ctab + cfirst[c], h0, cnp[c], d_cnb + (size_t)cfirst[c] * 27, h0.Z, b->gamma,
                               b->courant, dxi, act, d_part, d_cnt, d_cdt + c, b->d_err, st));
             ++b->launches;
         }

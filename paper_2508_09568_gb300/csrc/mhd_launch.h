@@ -86,11 +86,13 @@ struct PrecisionKernels {
     cudaError_t (*cfl_patch)(const void* U0, const void* U1, const PatchDev* patches, const int* list, int nlist,
                              const int* nlist_dev, int grid_y, const int* slice, double gamma, const double dxi[3],
                              const int act[3], unsigned long long* rate_max, unsigned* err, cudaStream_t s);
-    // guard fill + CFL dt in one pass (regular grids: nboff the neighbour table, Zp the padded
-    // z extent); partial: npatch * Zp reals; counter: one zeroed unsigned
-    cudaError_t (*fill_cfl)(void* U, const PatchDev* patches, int npatch, const int64_t* nboff, int Zp, double gamma,
-                            double courant, const double dxi[3], const int act[3], void* partial, unsigned* counter,
-                            double* dt_out, unsigned* err, cudaStream_t s);
+    // guard fill + CFL dt in one pass (regular grids: h0 a host copy of the patches' common
+    // geometry, nboff the neighbour table, Zp the padded z extent); partial: npatch * Zp
+    // reals; counter: one zeroed unsigned
+    cudaError_t (*fill_cfl)(void* U, const PatchDev* patches, const PatchDev& h0, int npatch, const int64_t* nboff,
+                            int Zp, double gamma, double courant, const double dxi[3], const int act[3], void* partial,
+                            unsigned* counter, double* dt_out, unsigned* err, cudaStream_t s);
+    cudaError_t (*prepare_fill_cfl)();   // opt the staged fill + CFL pass in to its shared memory
 };
 
 const PrecisionKernels& kernels_f32();
