@@ -54,7 +54,9 @@ MHD_HD R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
     const R cat2 = fma_(bt1, bt1, bt2 * bt2) * rho_inv;
     const R d = cs2 - can2;
     const R disc = fma_(d, d, cat2 * fma_(R(2), cs2 + can2, cat2));
-    return rsqrt_(R(0.5) * (cs2 + can2 + cat2 + rsqrt_(disc)));
+    // 1/2 (s + sqrt(disc)) as one fused step after the square root (halving is exact, so
+    // this rounds as 1/2 * (s + sqrt(disc)) does)
+    return rsqrt_(fma_(R(0.5), rsqrt_(disc), R(0.5) * (cs2 + can2 + cat2)));
 }
 
 // Primitive state from the conserved one; the cell-centred field is the mean of the two
@@ -94,6 +96,28 @@ MHD_HD void hancock(const R q[8], const R D[3][8], R hdt, R gamma, R out[5]) {
         // (1/rho)[d_c P + B_a d_c B_a + B_b d_c B_b - B_a d_a B_c - B_b d_b B_c]
         const R lor = fma_(q[Q_BX + a], D[c][Q_BX + a] - D[a][Q_BX + c],
                            fma_(q[Q_BX + b], D[c][Q_BX + b] - D[b][Q_BX + c], D[c][Q_P]));
+        out[1 + c] = q[Q_U + c] - hdt * fma_(lor, ri, adv(Q_U + c));
+    }
+}
+
+// The same half step from the undivided slopes dW[d][k] and the inverse cell sizes dxi[d]
+// (D = dW * dxi folded into the products that use it; equal to hancock up to rounding).
+// The step kernel's prep uses this form: one multiply less on each slope's path.
+template <typename R>
+MHD_HD void hancock_dw(const R q[8], const R dW[3][8], const R dxi[3], R hdt, R gamma, R out[5]) {
+    const R u = q[Q_U], v = q[Q_V], w = q[Q_W], rho = q[Q_RHO], P = q[Q_P];
+    const R us = u * dxi[0], vs = v * dxi[1], ws = w * dxi[2];
+    const R divu = fma_(dxi[0], dW[0][Q_U], fma_(dxi[1], dW[1][Q_V], dxi[2] * dW[2][Q_W]));
+    const R ri = rdiv(R(1), rho);
+    auto adv = [&](int k) { return fma_(us, dW[0][k], fma_(vs, dW[1][k], ws * dW[2][k])); };
+    out[0] = rho - hdt * fma_(rho, divu, adv(Q_RHO));
+    out[4] = P - hdt * fma_(gamma * P, divu, adv(Q_P));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = (c + 1) % 3, b = (c + 2) % 3;
+        const R ja = fma_(dxi[c], dW[c][Q_BX + a], -(dxi[a] * dW[a][Q_BX + c]));
+        const R jb = fma_(dxi[c], dW[c][Q_BX + b], -(dxi[b] * dW[b][Q_BX + c]));
+        const R lor = fma_(q[Q_BX + a], ja, fma_(q[Q_BX + b], jb, dxi[c] * dW[c][Q_P]));
         out[1 + c] = q[Q_U + c] - hdt * fma_(lor, ri, adv(Q_U + c));
     }
 }
@@ -149,7 +173,9 @@ MHD_HD void hlld(const R L[7], const R Rt[7], R bn, R gamma, R gm1i, R eps, R F[
     const R sql = rsqrt_(rsl), sqr = rsqrt_(rsr);
     const R abn = rabs(bn);
     const R ssl = sm - rdiv(abn, sql), ssr = sm + rdiv(abn, sqr);
-    const R sgn = sel(gt(bn, zero), R(1), sel(lt(bn, zero), R(-1), zero));
+    // sign of bn (+-1; at bn = 0 the double-star region has zero width, ssl = sm = ssr, and
+    // is never the one selected, so its value there does not matter)
+    const R sgn = copysign(R(1), bn);
     const R isum = rdiv(R(1), sql + sqr);
     const R vss = fma_(sql, vsl, fma_(sqr, vsr, (bysr - bysl) * sgn)) * isum;
     const R wss = fma_(sql, wsl, fma_(sqr, wsr, (bzsr - bzsl) * sgn)) * isum;

@@ -47,8 +47,11 @@ MHD_HD bool mnot(bool a) { return !a; }
 template <typename R>
 MHD_HD R sel(bool m, R a, R b) { return m ? a : b; }
 
-template <typename R>
-MHD_HD R rabs(R x) { return x < R(0) ? -x : x; }
+// |x| (the sign of a zero result is +0; the scheme only compares magnitudes or divides
+// them, so it never depends on that sign).  fabs lets the compiler fold |.| into the
+// consuming instruction as an operand modifier instead of a compare and a select.
+MHD_HD float rabs(float x) { return fabsf(x); }
+MHD_HD double rabs(double x) { return fabs(x); }
 
 MHD_HD float rsqrt_(float x) { return sqrtf(x); }
 MHD_HD double rsqrt_(double x) { return sqrt(x); }

@@ -285,13 +285,8 @@ __device__ __forceinline__ void prep_cell(const PrepCtx<R, C>& X, int i, int j, 
     const R bzh0 = bz + tz0, bzh1 = (C::AZ ? wv(X, 10, i, j, 1) : bz) + tz1;
 
     // a5: Hancock predictor
-    R D[3][8];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) D[d][k] = dW[d][k] * X.dxi[d];
     R hq[5];
-    hancock(q, D, X.hdt, X.gamma, hq);
+    hancock_dw(q, dW, X.dxi, X.hdt, X.gamma, hq);
 
 #pragma unroll
     for (int k = 0; k < 5; ++k) Pslot[PV_WH(k) * C::PSZ + pid] = hq[k];
