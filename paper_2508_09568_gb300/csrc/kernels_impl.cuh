@@ -89,14 +89,16 @@ static cudaError_t launch_fill_cfl(void* U, const PatchDev* patches, const Patch
                                   cudaStream_t s) {
     const unsigned grid = (unsigned)npatch * (unsigned)Zp;
     const size_t smem = fill_cfl_staged_smem<R>(h0.X, h0.Y, h0.nx, h0.ny, h0.gx, h0.gy);
+    // constants in the kernel's precision, rounded here once (as the kernel would round them)
+    const R g = R(gamma), gm1 = R(gamma - 1.0), d0 = R(dxi[0]), d1 = R(dxi[1]), d2 = R(dxi[2]);
     if (fill_cfl_staged_fits<R>(h0))
-        fill_cfl_staged_kernel<R><<<grid, 256, smem, s>>>(static_cast<R*>(U), patches, nboff, Zp, gamma, courant,
-                                                          dxi[0], dxi[1], dxi[2], act[1], act[2],
-                                                          static_cast<R*>(partial), counter, dt_out, err);
+        fill_cfl_staged_kernel<R><<<grid, 256, smem, s>>>(static_cast<R*>(U), patches, nboff, Zp, g, gm1, courant, d0,
+                                                          d1, d2, act[1], act[2], static_cast<R*>(partial), counter,
+                                                          dt_out, err);
     else
-        fill_cfl_grid_kernel<R><<<grid, 128, 0, s>>>(static_cast<R*>(U), patches, nboff, Zp, gamma, courant, dxi[0],
-                                                     dxi[1], dxi[2], act[1], act[2], static_cast<R*>(partial),
-                                                     counter, dt_out, err);
+        fill_cfl_grid_kernel<R><<<grid, 128, 0, s>>>(static_cast<R*>(U), patches, nboff, Zp, g, gm1, courant, d0, d1,
+                                                     d2, act[1], act[2], static_cast<R*>(partial), counter, dt_out,
+                                                     err);
     return cudaGetLastError();
 }
 

@@ -272,7 +272,7 @@ __global__ void cfl_kernel(CflArgs<R> a) {
             for (int x = lane; x < pt.nx; x += 32) {
                 const R rate = cell_rate(row + x, vol, sy, sz, a.act[1] != 0, a.act[2] != 0, gamma, gm1, dxi0,
                                          dxi1, dxi2);
-                if (!isfinite((double)rate)) bad = true;
+                if (!finite_(rate)) bad = true;
                 else vmax = rate > vmax ? rate : vmax;
             }
         }
@@ -311,9 +311,9 @@ __global__ void cfl_kernel(CflArgs<R> a) {
 // ---------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
-                                                           const int64_t* __restrict__ nboff, int Zp, double gamma_d,
-                                                           double courant, double dxi0_d, double dxi1_d,
-                                                           double dxi2_d, int act1, int act2, R* partial,
+                                                           const int64_t* __restrict__ nboff, int Zp, R gamma, R gm1,
+                                                           double courant, R dxi0, R dxi1, R dxi2, int act1,
+                                                           int act2, R* partial,
                                                            unsigned* counter, double* dt_out, unsigned* err) {
     __shared__ R red[32];
     __shared__ bool last;
@@ -371,8 +371,6 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
     R vmax = R(0);
     bool bad = false;
     if (!zghost) {
-        const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
-        const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
         const bool top = iz + 1 == pt.nz;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         // each warp takes RR rows at a time, every load of the RR cells before the rates
@@ -397,7 +395,7 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
                     if (y0 + r >= pt.ny) continue;
                     const R rate = cell_rate_vals(u[r], bxh[r], byh[r], bzh[r], act1 != 0, act2 != 0, gamma, gm1, dxi0,
                                                   dxi1, dxi2);
-                    if (!isfinite((double)rate)) bad = true;
+                    if (!finite_(rate)) bad = true;
                     else vmax = rate > vmax ? rate : vmax;
                 }
             }
@@ -428,30 +426,47 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
 }
 
 // ---------------------------------------------------------------------------------------
-// a1 + a2 fused and staged through shared memory, for regular grids whose plane fits (the
-// ghost values and the dt of fill_cfl_grid_kernel, bitwise).  One CTA per padded z-plane
-// of a patch puts every global load of its plane in flight at once: an interior plane
-// brings its own padded plane (8 contiguous blocks of X*Y reals, one per variable) into
-// shared memory with bulk copies (TMA) on an mbarrier, and the sources of its ghost cells,
-// the high x- and y-faces of its last column and row (the sources of the ghost cells
-// standing there) and the high z-faces (the next plane, or the neighbour above) with
-// element copies (cp.async); a z-ghost plane brings only its ghost sources.  The CTA then
-// waits for DRAM once, holding no registers for the data in flight, writes the ghost cells
-// and takes the rates from shared memory.  Only this CTA writes its plane's ghost cells,
-// and it does so after the copies have landed, so no copy reads a cell being written.
-// The wait on the bulk copies is bounded (one second of %globaltimer): past it the CTA
-// sets ERR_TIMEOUT, waits once more (bounded) for its copies, skips its work and reports
-// an infinite rate, so the launch still completes and the dt is not a valid one.
-// Dynamic shared memory, in elements: interior plane PL[8][X*Y] G[8][ng] FX[ny] FY[nx]
-// FZ[ny*nx] (ng = 2 gy X + 2 gx ny); z-ghost plane G[8][X*Y] (fill_cfl_staged_smem).
-// A plane whose address or byte size is not a multiple of 16 (no bulk copy) is brought in
-// with element copies of its interior cells instead.
+// a1 + a2 fused, with the interior staged through shared memory, for regular grids whose
+// plane fits (the ghost values and the dt of fill_cfl_grid_kernel, bitwise).  One CTA per
+// padded z-plane of a patch.  An interior plane brings the rows of its own plane that hold
+// interior cells (rows gy .. gy+ny-1 of each variable, rounded out to 16-byte bounds: one
+// contiguous block per variable) into shared memory with bulk copies (TMA) on an mbarrier,
+// and the high x- and y-faces of its last column and row and the high z-faces (the next
+// plane, or the neighbour above) with element copies (cp.async).  While those are in
+// flight, every thread copies its ghost cells of the plane through registers, three cells
+// (FP64: one) at a time with all their loads before their stores, the sources found from the patch's
+// 27 neighbour offsets held in shared memory; a z-ghost plane only copies ghost cells.
+// Then the CTA waits once (each thread for its element copies, one thread on the mbarrier,
+// then a barrier) and takes the rates of its interior cells from shared memory.  Ghost
+// sources are interior cells and destinations ghost cells, and the staged rows are
+// interior cells and the high faces, which no CTA writes, so nothing read here is written
+// by the launch.
+// The wait on the bulk copies is bounded (one second of %globaltimer; the waiting thread
+// is suspended between polls): past it the CTA sets ERR_TIMEOUT, waits once more
+// (bounded) for its copies, skips the rates and reports an infinite rate, so the launch
+// still completes and the dt is not a valid one.
+// Dynamic shared memory, in elements: PL[8][r1 - r0] FX[ny] FY[nx] FZ[ny*nx]
+// (fill_cfl_staged_smem).  Rows whose address or byte size, or a plane whose X*Y reals,
+// are not a multiple of 16 bytes (no bulk copy) are brought in with element copies of the
+// interior cells instead.
 // ---------------------------------------------------------------------------------------
+
+// elements [r0, r1) of a padded plane staged for the rates: rows gy .. gy+ny-1 rounded out
+// to 16-byte bounds (within the plane)
+template <typename R>
+__host__ __device__ inline void fill_cfl_staged_rows(int X, int Y, int ny, int gy, int& r0, int& r1) {
+    constexpr int EQ = 16 / (int)sizeof(R);
+    r0 = (gy * X) / EQ * EQ;
+    r1 = ((gy + ny) * X + EQ - 1) / EQ * EQ;
+    if (r1 > X * Y) r1 = X * Y;
+}
+
 template <typename R>
 __host__ __device__ inline size_t fill_cfl_staged_smem(int X, int Y, int nx, int ny, int gx, int gy) {
-    const size_t xy = (size_t)X * Y, ng = (size_t)2 * gy * X + (size_t)2 * gx * ny, nin = (size_t)nx * ny;
-    const size_t inner = 8 * xy + 8 * ng + ny + nx + nin, outer = 8 * xy;
-    return (inner > outer ? inner : outer) * sizeof(R);
+    (void)gx;
+    int r0, r1;
+    fill_cfl_staged_rows<R>(X, Y, ny, gy, r0, r1);
+    return ((size_t)8 * (r1 - r0) + ny + nx + (size_t)nx * ny) * sizeof(R);
 }
 // planes whose staging needs more than this take fill_cfl_grid_kernel (two CTAs per SM fit)
 constexpr size_t FILL_CFL_STAGED_MAX_SMEM = 113 * 1024;
@@ -476,149 +491,186 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// phase 0 of the mbarrier at bar completed within limit_ns (false: gave up)
+// phase 0 of the mbarrier at bar completed within limit_ns (false: gave up); between polls
+// the thread is suspended (up to 20 us, or until the phase completes)
 __device__ __forceinline__ bool mbar_wait0(unsigned bar, uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
     for (;;) {
         unsigned done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(bar)
+            : "r"(bar), "r"(20000u)
             : "memory");
         if (done) return true;
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
+// (x, y) of the items k = k0, k0 + S, k0 + 2S, ... of a row-major index space of rows w
+// wide, stepped without a division per item (one division per thread at the start)
+struct Walk2 {
+    int x, y, sx, sy, w;
+    __device__ __forceinline__ Walk2(int k0, int w_, int S) : w(w_) {
+        y = k0 / w;
+        x = k0 - y * w;
+        sy = S / w;
+        sx = S - sy * w;
+    }
+    __device__ __forceinline__ void next() {
+        x += sx;
+        y += sy;
+        if (x >= w) {
+            x -= w;
+            ++y;
+        }
+    }
+};
+
 template <typename R>
-__global__ void __launch_bounds__(256) fill_cfl_staged_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
-                                                             const int64_t* __restrict__ nboff, int Zp, double gamma_d,
-                                                             double courant, double dxi0_d, double dxi1_d,
-                                                             double dxi2_d, int act1, int act2, R* partial,
-                                                             unsigned* counter, double* dt_out, unsigned* err) {
+__global__ void __launch_bounds__(256, 4) fill_cfl_staged_kernel(R* __restrict__ U, const PatchDev* __restrict__ patches,
+                                                             const int64_t* __restrict__ nboff, int Zp, R gamma, R gm1,
+                                                             double courant, R dxi0, R dxi1, R dxi2, int act1,
+                                                             int act2, R* partial, unsigned* counter, double* dt_out,
+                                                             unsigned* err) {
     extern __shared__ __align__(128) unsigned char fc_smem[];
     __shared__ R red[32];
     __shared__ bool last;
+    __shared__ int s_ok;
+    __shared__ int64_t s_nb[27];
     __shared__ __align__(8) uint64_t bar_mem;
     const int p = blockIdx.x / Zp, z = blockIdx.x - p * Zp;
     const PatchDev pt = patches[p];
-    const int64_t* nb = nboff + (int64_t)p * 27;
     const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy, nx = pt.nx, ny = pt.ny;
     const int XY = X * Y;
     const int64_t vol = (int64_t)XY * pt.Z;
     const int iz = z - pt.gz;
     const bool zghost = iz < 0 || iz >= pt.nz;
     const int nfull = zghost ? XY : 2 * gy * X;
-    const int ncnt = zghost ? XY : nfull + ny * 2 * gx;
     const int nin = nx * ny;
     R* plane = U + pt.off + (int64_t)z * XY;
-    R* PL = reinterpret_cast<R*>(fc_smem);
-    R* G = zghost ? PL : PL + 8 * XY;
-    R* FX = G + 8 * ncnt;
+    int r0, r1;
+    fill_cfl_staged_rows<R>(X, Y, ny, gy, r0, r1);
+    const int NR = r1 - r0;
+    R* PL = reinterpret_cast<R*>(fc_smem);   // PL[q * NR + c - r0]: element c of variable q's plane
+    R* FX = PL + 8 * NR;
     R* FY = FX + ny;
     R* FZ = FY + nx;
     const unsigned bar = static_cast<unsigned>(__cvta_generic_to_shared(&bar_mem));
-    // plane coordinates of the k-th ghost cell of the plane (the order of fill_grid_kernel)
-    auto coord = [&](int k, int& x, int& y) {
-        if (k < nfull) {
-            const int r = k / X;
-            x = k - r * X;
-            y = zghost ? r : (r < gy ? r : ny + r);
-        } else {
-            const int k2 = k - nfull;
-            const int r = k2 / (2 * gx), c = k2 - r * (2 * gx);
-            y = gy + r;
-            x = c < gx ? c : nx + c;
-        }
-    };
-    // 1. every load of the plane in flight
-    const bool bulk = !zghost && ((reinterpret_cast<uintptr_t>(plane) | ((size_t)XY * sizeof(R))) & 15) == 0;
+    // the patch's neighbour offsets, read once per CTA
+    if (threadIdx.x < 27) s_nb[threadIdx.x] = nboff[(int64_t)p * 27 + threadIdx.x];
+    const bool bulk = !zghost && ((reinterpret_cast<uintptr_t>(plane + r0) | ((size_t)NR * sizeof(R)) |
+                                   ((size_t)XY * sizeof(R))) & 15) == 0;
+    if (bulk && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    // 1. the staged rows and high faces in flight
     if (bulk) {
         if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned bytes = (unsigned)(XY * sizeof(R));
+            const unsigned bytes = (unsigned)(NR * sizeof(R));
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(8 * bytes)
                          : "memory");
 #pragma unroll 1
             for (int q = 0; q < 8; ++q) {
-                const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(PL + q * XY));
+                const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(PL + q * NR));
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-                    "l"(plane + q * vol), "r"(bytes), "r"(bar)
+                    "l"(plane + q * vol + r0), "r"(bytes), "r"(bar)
                     : "memory");
             }
         }
     } else if (!zghost) {
-        for (int k = threadIdx.x; k < nin; k += blockDim.x) {
-            const int y = k / nx, x = k - y * nx;
-            const int c = (y + gy) * X + x + gx;
+        Walk2 w(threadIdx.x, nx, blockDim.x);
+        for (int k = threadIdx.x; k < nin; k += blockDim.x, w.next()) {
+            const int c = (w.y + gy) * X + w.x + gx;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) cp_async_elem_aux(PL + q * XY + c, plane + q * vol + c);
+            for (int q = 0; q < 8; ++q) cp_async_elem_aux(PL + q * NR + c - r0, plane + q * vol + c);
         }
-    }
-    for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
-        int x, y;
-        coord(k, x, y);
-        const R* src = U + neighbour_source(pt, nb, x - gx, y - gy, iz);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) cp_async_elem_aux(G + q * ncnt + k, src + q * vol);
     }
     if (!zghost) {
         const bool top = iz + 1 == pt.nz;
-        if (act2)
-            for (int k = threadIdx.x; k < nin; k += blockDim.x) {
-                const int y = k / nx, x = k - y * nx;
-                cp_async_elem_aux(FZ + k, top ? U + 7 * vol + neighbour_source(pt, nb, x, y, pt.nz)
-                                              : plane + 7 * vol + (int64_t)XY + (int64_t)(y + gy) * X + x + gx);
-            }
+        if (act2) {
+            Walk2 w(threadIdx.x, nx, blockDim.x);
+            for (int k = threadIdx.x; k < nin; k += blockDim.x, w.next())
+                cp_async_elem_aux(FZ + k, top ? U + 7 * vol + neighbour_source(pt, s_nb, w.x, w.y, pt.nz)
+                                              : plane + 7 * vol + (int64_t)XY + (int64_t)(w.y + gy) * X + w.x + gx);
+        }
         for (int k = threadIdx.x; k < ny + nx; k += blockDim.x) {
-            if (k < ny) cp_async_elem_aux(FX + k, U + 5 * vol + neighbour_source(pt, nb, nx, k, iz));
-            else if (act1) cp_async_elem_aux(FY + (k - ny), U + 6 * vol + neighbour_source(pt, nb, k - ny, ny, iz));
+            if (k < ny) cp_async_elem_aux(FX + k, U + 5 * vol + neighbour_source(pt, s_nb, nx, k, iz));
+            else if (act1) cp_async_elem_aux(FY + (k - ny), U + 6 * vol + neighbour_source(pt, s_nb, k - ny, ny, iz));
         }
     }
+    // 2. the ghost cells of the plane through registers, NC per thread at a time (index k
+    // over the full rows, then the x-ghost runs of the interior rows), all loads of a group
+    // before its stores
+    {
+        constexpr int NC = sizeof(R) == 4 ? 3 : 1;
+        const int ncnt = zghost ? XY : nfull + ny * 2 * gx;
+        for (int k0 = threadIdx.x; k0 < ncnt; k0 += NC * blockDim.x) {
+            R v[NC][8];
+            R* dst[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int k = k0 + c * (int)blockDim.x;
+                dst[c] = nullptr;
+                if (k < ncnt) {
+                    int x, y;
+                    if (k < nfull) {
+                        const int r = k / X;
+                        x = k - r * X;
+                        y = zghost ? r : (r < gy ? r : ny + r);
+                    } else {
+                        const int k2 = k - nfull;
+                        const int r = k2 / (2 * gx), cc = k2 - r * (2 * gx);
+                        y = gy + r;
+                        x = cc < gx ? cc : nx + cc;
+                    }
+                    const R* src = U + neighbour_source(pt, s_nb, x - gx, y - gy, iz);
+                    dst[c] = plane + y * X + x;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[c][q] = src[q * vol];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (dst[c]) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dst[c][q * vol] = v[c][q];
+                }
+        }
+    }
+    // 3. one wait: each thread for its element copies, thread 0 for the bulk copies (the
+    // barrier then publishes both)
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    bool ok = true;
-    if (bulk) ok = mbar_wait0(bar, 1000000000ull);
-    ok = __syncthreads_and(ok);
+    if (threadIdx.x == 0) s_ok = bulk ? (int)mbar_wait0(bar, 1000000000ull) : 1;
+    __syncthreads();
     R vmax = R(0);
     bool bad = false;
-    if (!ok) {
+    if (!s_ok) {
         // copies that did not land in time: wait once more (bounded) so that none is still
         // writing this CTA's shared memory when it exits, and report
-        mbar_wait0(bar, 1000000000ull);
-        if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
-        vmax = R(INFINITY);
-    } else {
-        // 2. the ghost cells
-        for (int k = threadIdx.x; k < ncnt; k += blockDim.x) {
-            int x, y;
-            coord(k, x, y);
-            R* d = plane + (int64_t)y * X + x;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) d[q * vol] = G[q * ncnt + k];
+        if (threadIdx.x == 0) {
+            mbar_wait0(bar, 1000000000ull);
+            atomicOr(err, ERR_TIMEOUT);
         }
-        // 3. the rates of the interior cells
-        if (!zghost) {
-            const R gamma = R(gamma_d), gm1 = R(gamma_d - 1.0);
-            const R dxi0 = R(dxi0_d), dxi1 = R(dxi1_d), dxi2 = R(dxi2_d);
-            for (int k = threadIdx.x; k < nin; k += blockDim.x) {
-                const int y = k / nx, x = k - y * nx;
-                const int c = (y + gy) * X + x + gx;
-                R u[8];
+        vmax = R(INFINITY);
+    } else if (!zghost) {
+        // 4. the rates of the interior cells
+        Walk2 w(threadIdx.x, nx, blockDim.x);
+        for (int k = threadIdx.x; k < nin; k += blockDim.x, w.next()) {
+            const int y = w.y, x = w.x;
+            const int c = (y + gy) * X + x + gx - r0;
+            R u[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) u[q] = PL[q * XY + c];
-                const R bxh = x + 1 < nx ? PL[5 * XY + c + 1] : FX[y];
-                const R byh = act1 ? (y + 1 < ny ? PL[6 * XY + c + X] : FY[x]) : R(0);
-                const R bzh = act2 ? FZ[k] : R(0);
-                const R rate = cell_rate_vals(u, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
-                if (!isfinite((double)rate)) bad = true;
-                else vmax = rate > vmax ? rate : vmax;
-            }
+            for (int q = 0; q < 8; ++q) u[q] = PL[q * NR + c];
+            const R bxh = x + 1 < nx ? PL[5 * NR + c + 1] : FX[y];
+            const R byh = act1 ? (y + 1 < ny ? PL[6 * NR + c + X] : FY[x]) : R(0);
+            const R bzh = act2 ? FZ[k] : R(0);
+            const R rate = cell_rate_vals(u, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
+            if (!finite_(rate)) bad = true;
+            else vmax = rate > vmax ? rate : vmax;
         }
     }
     if (bad) atomicOr(err, ERR_PHYS);
@@ -845,7 +897,7 @@ __global__ void cfl_patch_kernel(const R* __restrict__ U0, const R* __restrict__
             const int x = k % pt.nx + pt.gx, y = (k / pt.nx) % pt.ny + pt.gy, z = k / (pt.nx * pt.ny) + pt.gz;
             const R* c = base + ((int64_t)z * pt.Y + y) * pt.X + x;
             const R rate = cell_rate(c, vol, pt.X, pt.X * pt.Y, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
-            if (!isfinite((double)rate)) bad = true;
+            if (!finite_(rate)) bad = true;
             else vmax = rate > vmax ? rate : vmax;
         }
         if (bad) atomicOr(err, ERR_PHYS);

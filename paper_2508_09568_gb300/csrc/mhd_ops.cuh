@@ -69,6 +69,10 @@ MHD_HD float rdiv(float a, float b) {
 }
 MHD_HD double rdiv(double a, double b) { return a / b; }
 
+// x is finite (tested in its own precision: no conversion to double)
+MHD_HD bool finite_(float x) { return isfinite(x); }
+MHD_HD bool finite_(double x) { return isfinite(x); }
+
 // Larger / smaller of two values (NaN operands are not propagated; the scheme's results
 // are checked for finiteness where they are written).
 MHD_HD float fmax_(float a, float b) { return fmaxf(a, b); }

@@ -440,7 +440,7 @@ __device__ __forceinline__ void stage_update(const StepSmem<R, C>& S, const R* _
         nv[7] = Ub[7 * vol] + dbz;
 #pragma unroll
         for (int v = 0; v < 8; ++v) Un[v * vol] = nv[v];
-        if (!(nv[0] > R(0)) || !isfinite((double)nv[4])) atomicOr(err, ERR_PHYS);
+        if (!(nv[0] > R(0)) || !finite_(nv[4])) atomicOr(err, ERR_PHYS);
     }
 }
 
