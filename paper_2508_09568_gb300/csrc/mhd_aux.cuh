@@ -430,12 +430,14 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
 // plane fits (the ghost values and the dt of fill_cfl_grid_kernel, bitwise).  One CTA per
 // padded z-plane of a patch.  An interior plane brings the rows of its own plane that hold
 // interior cells (rows gy .. gy+ny-1 of each variable, rounded out to 16-byte bounds: one
-// contiguous block per variable) into shared memory with bulk copies (TMA) on an mbarrier,
-// and the high x- and y-faces of its last column and row and the high z-faces (the next
-// plane, or the neighbour above) with element copies (cp.async).  While those are in
+// contiguous block per variable) and the same rows of B_z in the plane above (the cells'
+// high z-faces) into shared memory with bulk copies (TMA) on an mbarrier, and the high x-
+// and y-faces of its last column and row, and for the top interior plane the high z-faces
+// from the neighbour above, with element copies (cp.async).  While those are in
 // flight, every thread copies its ghost cells of the plane through registers, three cells
-// (FP64: one) at a time with all their loads before their stores, the sources found from the patch's
-// 27 neighbour offsets held in shared memory; a z-ghost plane only copies ghost cells.
+// (FP64: one) at a time with all their loads before their stores, the sources found from
+// the patch's 27 neighbour offsets held in shared memory; a z-ghost plane only copies
+// ghost cells.
 // Then the CTA waits once (each thread for its element copies, one thread on the mbarrier,
 // then a barrier) and takes the rates of its interior cells from shared memory.  Ghost
 // sources are interior cells and destinations ghost cells, and the staged rows are
@@ -445,7 +447,7 @@ __global__ void __launch_bounds__(128) fill_cfl_grid_kernel(R* __restrict__ U, c
 // is suspended between polls): past it the CTA sets ERR_TIMEOUT, waits once more
 // (bounded) for its copies, skips the rates and reports an infinite rate, so the launch
 // still completes and the dt is not a valid one.
-// Dynamic shared memory, in elements: PL[8][r1 - r0] FX[ny] FY[nx] FZ[ny*nx]
+// Dynamic shared memory, in elements: PL[8][r1 - r0] PZ[r1 - r0] FX[ny] FY[nx]
 // (fill_cfl_staged_smem).  Rows whose address or byte size, or a plane whose X*Y reals,
 // are not a multiple of 16 bytes (no bulk copy) are brought in with element copies of the
 // interior cells instead.
@@ -466,7 +468,7 @@ __host__ __device__ inline size_t fill_cfl_staged_smem(int X, int Y, int nx, int
     (void)gx;
     int r0, r1;
     fill_cfl_staged_rows<R>(X, Y, ny, gy, r0, r1);
-    return ((size_t)8 * (r1 - r0) + ny + nx + (size_t)nx * ny) * sizeof(R);
+    return ((size_t)9 * (r1 - r0) + ny + nx) * sizeof(R);
 }
 // planes whose staging needs more than this take fill_cfl_grid_kernel (two CTAs per SM fit)
 constexpr size_t FILL_CFL_STAGED_MAX_SMEM = 113 * 1024;
@@ -553,9 +555,9 @@ __global__ void __launch_bounds__(256, 4) fill_cfl_staged_kernel(R* __restrict__
     fill_cfl_staged_rows<R>(X, Y, ny, gy, r0, r1);
     const int NR = r1 - r0;
     R* PL = reinterpret_cast<R*>(fc_smem);   // PL[q * NR + c - r0]: element c of variable q's plane
-    R* FX = PL + 8 * NR;
+    R* PZ = PL + 8 * NR;   // PZ[c - r0]: the high z-face of the cell at c (B_z of the plane above)
+    R* FX = PZ + NR;
     R* FY = FX + ny;
-    R* FZ = FY + nx;
     const unsigned bar = static_cast<unsigned>(__cvta_generic_to_shared(&bar_mem));
     // the patch's neighbour offsets, read once per CTA
     if (threadIdx.x < 27) s_nb[threadIdx.x] = nboff[(int64_t)p * 27 + threadIdx.x];
@@ -566,18 +568,22 @@ __global__ void __launch_bounds__(256, 4) fill_cfl_staged_kernel(R* __restrict__
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
-    // 1. the staged rows and high faces in flight
+    // 1. the staged rows and high faces in flight (below the top interior plane the high
+    // z-faces are variable 7 of the next plane's staged rows: a ninth bulk copy)
+    const bool top = iz + 1 == pt.nz;
+    const int nbulk = (act2 && !top) ? 9 : 8;
     if (bulk) {
         if (threadIdx.x == 0) {
             const unsigned bytes = (unsigned)(NR * sizeof(R));
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(8 * bytes)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(nbulk * bytes)
                          : "memory");
 #pragma unroll 1
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < nbulk; ++q) {
                 const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(PL + q * NR));
+                const R* src = q < 8 ? plane + q * vol + r0 : plane + 7 * vol + XY + r0;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(d),
-                    "l"(plane + q * vol + r0), "r"(bytes), "r"(bar)
+                    "l"(src), "r"(bytes), "r"(bar)
                     : "memory");
             }
         }
@@ -587,15 +593,15 @@ __global__ void __launch_bounds__(256, 4) fill_cfl_staged_kernel(R* __restrict__
             const int c = (w.y + gy) * X + w.x + gx;
 #pragma unroll
             for (int q = 0; q < 8; ++q) cp_async_elem_aux(PL + q * NR + c - r0, plane + q * vol + c);
+            if (act2 && !top) cp_async_elem_aux(PZ + c - r0, plane + 7 * vol + XY + c);
         }
     }
     if (!zghost) {
-        const bool top = iz + 1 == pt.nz;
-        if (act2) {
+        if (act2 && top) {
             Walk2 w(threadIdx.x, nx, blockDim.x);
             for (int k = threadIdx.x; k < nin; k += blockDim.x, w.next())
-                cp_async_elem_aux(FZ + k, top ? U + 7 * vol + neighbour_source(pt, s_nb, w.x, w.y, pt.nz)
-                                              : plane + 7 * vol + (int64_t)XY + (int64_t)(w.y + gy) * X + w.x + gx);
+                cp_async_elem_aux(PZ + (w.y + gy) * X + w.x + gx - r0,
+                                  U + 7 * vol + neighbour_source(pt, s_nb, w.x, w.y, pt.nz));
         }
         for (int k = threadIdx.x; k < ny + nx; k += blockDim.x) {
             if (k < ny) cp_async_elem_aux(FX + k, U + 5 * vol + neighbour_source(pt, s_nb, nx, k, iz));
@@ -667,7 +673,7 @@ __global__ void __launch_bounds__(256, 4) fill_cfl_staged_kernel(R* __restrict__
             for (int q = 0; q < 8; ++q) u[q] = PL[q * NR + c];
             const R bxh = x + 1 < nx ? PL[5 * NR + c + 1] : FX[y];
             const R byh = act1 ? (y + 1 < ny ? PL[6 * NR + c + X] : FY[x]) : R(0);
-            const R bzh = act2 ? FZ[k] : R(0);
+            const R bzh = act2 ? PZ[c] : R(0);
             const R rate = cell_rate_vals(u, bxh, byh, bzh, act1 != 0, act2 != 0, gamma, gm1, dxi0, dxi1, dxi2);
             if (!finite_(rate)) bad = true;
             else vmax = rate > vmax ? rate : vmax;

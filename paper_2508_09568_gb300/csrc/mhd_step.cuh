@@ -213,12 +213,13 @@ __device__ __forceinline__ R emf_n(const PrepCtx<R, C>& X, int e, int i, int j, 
     off(a, ai, aj, ak);
     off(b, bi, bj, bk);
     const int qa = Q_U + a, qb = Q_U + b;
-    const R va = R(0.25) * (wv(X, qa, i, j, dk) + wv(X, qa, i + ai, j + aj, dk + ak) +
-                            wv(X, qa, i + bi, j + bj, dk + bk) +
-                            wv(X, qa, i + ai + bi, j + aj + bj, dk + ak + bk));
-    const R vb = R(0.25) * (wv(X, qb, i, j, dk) + wv(X, qb, i + ai, j + aj, dk + ak) +
-                            wv(X, qb, i + bi, j + bj, dk + bk) +
-                            wv(X, qb, i + ai + bi, j + aj + bj, dk + ak + bk));
+    // (pairwise sums: two dependent additions instead of three)
+    const R va = R(0.25) * ((wv(X, qa, i, j, dk) + wv(X, qa, i + ai, j + aj, dk + ak)) +
+                            (wv(X, qa, i + bi, j + bj, dk + bk) +
+                             wv(X, qa, i + ai + bi, j + aj + bj, dk + ak + bk)));
+    const R vb = R(0.25) * ((wv(X, qb, i, j, dk) + wv(X, qb, i + ai, j + aj, dk + ak)) +
+                            (wv(X, qb, i + bi, j + bj, dk + bk) +
+                             wv(X, qb, i + ai + bi, j + aj + bj, dk + ak + bk)));
     const R Ba = R(0.5) * (wv(X, 8 + a, i, j, dk) + wv(X, 8 + a, i + bi, j + bj, dk + bk));
     const R Bb = R(0.5) * (wv(X, 8 + b, i, j, dk) + wv(X, 8 + b, i + ai, j + aj, dk + ak));
     return va * Bb - vb * Ba;
