@@ -229,9 +229,9 @@ __device__ __forceinline__ R cell_rate_vals(const R u[8], R bxh, R byh, R bzh, b
     R q[8];
     cons_to_prim(u[0], u[1], u[2], u[3], u[4], bxc, byc, bzc, gm1, q);
     const R ri = rdiv(R(1), q[Q_RHO]), gP = gamma * q[Q_P];
-    R rate = (rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc)) * dxi0;
-    if (act1) rate += (rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc)) * dxi1;
-    if (act2) rate += (rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc)) * dxi2;
+    R rate = mul_(rabs(q[Q_U]) + fast_speed(ri, gP, bxc, byc, bzc), dxi0);
+    if (act1) rate = fma_(rabs(q[Q_V]) + fast_speed(ri, gP, byc, bzc, bxc), dxi1, rate);
+    if (act2) rate = fma_(rabs(q[Q_W]) + fast_speed(ri, gP, bzc, bxc, byc), dxi2, rate);
     return rate;
 }
 

@@ -49,9 +49,10 @@ MHD_HD R limited(R a, R b, int limiter) {
 // as (cs^2 - can^2)^2 + cat^2 (2 (cs^2 + can^2) + cat^2) (identical, no cancellation).
 template <typename R>
 MHD_HD R fast_speed(R rho_inv, R gP, R bn, R bt1, R bt2) {
-    const R cs2 = gP * rho_inv;
-    const R can2 = bn * bn * rho_inv;
-    const R cat2 = fma_(bt1, bt1, bt2 * bt2) * rho_inv;
+    // (products that feed sums are unfusable: every kernel rounds the speed the same way)
+    const R cs2 = mul_(gP, rho_inv);
+    const R can2 = mul_(mul_(bn, bn), rho_inv);
+    const R cat2 = mul_(fma_(bt1, bt1, bt2 * bt2), rho_inv);
     const R d = cs2 - can2;
     const R disc = fma_(d, d, cat2 * fma_(R(2), cs2 + can2, cat2));
     // 1/2 (s + sqrt(disc)) as one fused step after the square root (halving is exact, so
@@ -69,9 +70,10 @@ MHD_HD void cons_to_prim(R rho, R mx, R my, R mz, R E, R bxc, R byc, R bzc, R gm
     q[Q_U] = u;
     q[Q_V] = v;
     q[Q_W] = w;
-    const R ke = R(0.5) * rho * fma_(u, u, fma_(v, v, w * w));
-    const R me = R(0.5) * fma_(bxc, bxc, fma_(byc, byc, bzc * bzc));
-    q[Q_P] = gm1 * (E - ke - me);
+    // P = (gamma-1) (E - rho |u|^2 / 2 - |B|^2 / 2), both subtractions fused
+    const R kin = fma_(u, u, fma_(v, v, w * w));
+    const R mag = fma_(bxc, bxc, fma_(byc, byc, bzc * bzc));
+    q[Q_P] = gm1 * fma_(R(-0.5), mag, fma_(R(-0.5) * rho, kin, E));
     q[Q_BX] = bxc;
     q[Q_BY] = byc;
     q[Q_BZ] = bzc;

@@ -5,6 +5,7 @@
 //
 // Helpers used by the scheme code for R = float, double:
 //   fma_(a, b, c) = a * b + c rounded once      sel(m, a, b) = m ? a : b
+//   mul_(a, b) = a * b, never fused
 //   lt / le / gt / ge -> mask                   mand / mor / mnot on masks
 //   rabs, rdiv (quotient), rsqrt_ (square root), fmax_ / fmin_ (larger / smaller value)
 #pragma once
@@ -30,6 +31,23 @@ MHD_HD double fma_(double a, double b, double c) {
     return __fma_rn(a, b, c);
 #else
     return fma(a, b, c);
+#endif
+}
+
+// a * b rounded on its own: never fused into a neighbouring addition by the compiler, so
+// that every kernel that evaluates the same expression rounds it the same way
+MHD_HD float mul_(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+MHD_HD double mul_(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
 #endif
 }
 

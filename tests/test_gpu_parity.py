@@ -122,12 +122,15 @@ def _outflow_box():
     return W.uniform_geometry([24, 16, 16], [8, 8, 8], dx=g0.dx, bc=bc), U, meta
 
 
-@pytest.mark.parametrize("case", ["box", "outflow", "ot", "sod"])
+@pytest.mark.parametrize("case", ["box", "outflow", "ot", "sod", "odd"])
 @pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
 def test_fused_fill_cfl_equals_separate_passes(case, dtype):
     """mhd_bunch_fill_cfl_device (one pass on regular grids) writes the ghost cells of the
-    guard fill and, bitwise, the dt of the separate CFL pass."""
+    guard fill and, bitwise, the dt of the separate CFL pass.  "odd": 5x7x6 patches, whose
+    padded planes (11x13 reals) are not a multiple of 16 bytes, so their rows come in by
+    element copies instead of bulk copies."""
     geom, U, meta = {"box": lambda: W.small_box(ncell=(16, 24, 16), patch=(8, 8, 8), seed=25),
+                     "odd": lambda: W.small_box(ncell=(10, 14, 12), patch=(5, 7, 6), seed=26),
                      "outflow": _outflow_box,
                      "ot": lambda: W.orszag_tang(ncell=64, patch=16),
                      "sod": lambda: W.sod(ncell=64, npatch=8)}[case]()
