@@ -44,11 +44,11 @@ OOC_BUDGET = 4 << 30                       # device budget of the out-of-core le
 # DRAM bytes (read + write) per cell-update of the fused step kernel, FP32, 32^3 patches,
 # per tile configuration (the two the autotuner picks between on this machine):
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of a 192^3 box of the
-# same patches and tiles (7,077,888 cells; 32 x 8: 451.85 MB + 233.20 MB, 16 x 16:
-# 453.31 MB + 236.44 MB).  Traffic scales with the number of patches, so a launch on the
+# same patches and tiles (7,077,888 cells; 32 x 8: 451.83 MB + 232.93 MB, 16 x 16:
+# 453.35 MB + 235.50 MB).  Traffic scales with the number of patches, so a launch on the
 # full box moves this many bytes per cell.  Valid for this kernel version only.
-STEP_DRAM_BYTES_PER_CELL = {(4, 32, (32, 8, 512)): (451.854592e6 + 233.195264e6) / 7077888,
-                            (4, 32, (16, 16, 512)): (453.313792e6 + 236.442880e6) / 7077888}
+STEP_DRAM_BYTES_PER_CELL = {(4, 32, (32, 8, 512)): (451.825920e6 + 232.927744e6) / 7077888,
+                            (4, 32, (16, 16, 512)): (453.351168e6 + 235.501568e6) / 7077888}
 
 
 def peaks():
