@@ -803,6 +803,8 @@ __global__ void __launch_bounds__(128) fill_interp_grid_kernel(R* __restrict__ U
                                                               const int* __restrict__ slice,
                                                               const double* __restrict__ t_old,
                                                               const double* __restrict__ t_cur) {
+    __shared__ double s_w[27];   // time weight of the slices of the patch in each direction
+    __shared__ int s_sq[27];     // its current slice
     const int nl = nlist_dev ? min(*nlist_dev, nlist) : nlist;
     const int z = blockIdx.x;
     for (int L = blockIdx.y; L < nl; L += gridDim.y) {
@@ -810,6 +812,16 @@ __global__ void __launch_bounds__(128) fill_interp_grid_kernel(R* __restrict__ U
         const PatchDev pt = patches[p];
         if (z >= pt.Z) continue;
         const int64_t* nb = nboff + (int64_t)p * 27;
+        // the weight depends on the source patch only: once per direction, not per ghost cell
+        // (an FP64 division per cell kept the small FP64 pipe busy)
+        __syncthreads();
+        if (threadIdx.x < 27) {
+            const int q = (int)(nb[threadIdx.x] / pstride);
+            const double den = t_cur[q] - t_old[q];
+            s_w[threadIdx.x] = den > 0.0 ? (t_cur[p] - t_old[q]) / den : 1.0;
+            s_sq[threadIdx.x] = slice[q];
+        }
+        __syncthreads();
         const int X = pt.X, Y = pt.Y, gx = pt.gx, gy = pt.gy;
         const int64_t vol = (int64_t)X * Y * pt.Z;
         const int iz = z - pt.gz;
@@ -817,7 +829,6 @@ __global__ void __launch_bounds__(128) fill_interp_grid_kernel(R* __restrict__ U
         const int nfull = zghost ? X * Y : 2 * gy * X;
         const int ncnt = zghost ? X * Y : nfull + pt.ny * 2 * gx;
         R* plane = (slice[p] ? U1 : U0) + pt.off + (int64_t)z * X * Y;
-        const double tp = t_cur[p];
         constexpr int NC = 4;
         for (int k0 = threadIdx.x; k0 < ncnt; k0 += NC * blockDim.x) {
             int64_t so[NC];
@@ -842,11 +853,10 @@ __global__ void __launch_bounds__(128) fill_interp_grid_kernel(R* __restrict__ U
                         x = cc < gx ? cc : pt.nx + cc;
                     }
                 }
-                so[c] = neighbour_source(pt, nb, on[c] ? x - gx : 0, on[c] ? y - gy : 0, on[c] ? iz : 0);
-                const int q = (int)(so[c] / pstride);
-                sq[c] = slice[q];
-                const double den = t_cur[q] - t_old[q];
-                w[c] = den > 0.0 ? (tp - t_old[q]) / den : 1.0;
+                int dir;
+                so[c] = neighbour_source_dir(pt, nb, on[c] ? x - gx : 0, on[c] ? y - gy : 0, on[c] ? iz : 0, dir);
+                sq[c] = s_sq[dir];
+                w[c] = s_w[dir];
                 dof[c] = (int64_t)y * X + x;
             }
             R vc[NC][8], vo[NC][8];

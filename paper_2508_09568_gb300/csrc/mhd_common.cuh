@@ -22,8 +22,9 @@ struct PatchDev {
 // copies: in the neighbouring patch (nb[27]: element offsets of the 27 neighbours,
 // direction (sx, sy, sz) at (sz+1)*9 + (sy+1)*3 + sx+1, periodic wrap applied), or the
 // nearest cell of the patch itself across an outflow box face (zero gradient).
-__device__ __forceinline__ int64_t neighbour_source(const PatchDev& pt, const int64_t* __restrict__ nb, int ix,
-                                                    int iy, int iz) {
+// (dir receives the table index (sz+1)*9 + (sy+1)*3 + sx+1 of the patch holding the source)
+__device__ __forceinline__ int64_t neighbour_source_dir(const PatchDev& pt, const int64_t* __restrict__ nb, int ix,
+                                                        int iy, int iz, int& dir) {
     int sx = 0, sy = 0, sz = 0;
     if (ix < 0) {
         if (pt.clamp & 1) ix = 0;
@@ -46,8 +47,13 @@ __device__ __forceinline__ int64_t neighbour_source(const PatchDev& pt, const in
         if (pt.clamp & 32) iz = pt.nz - 1;
         else { sz = 1; iz -= pt.nz; }
     }
-    return nb[(sz + 1) * 9 + (sy + 1) * 3 + (sx + 1)] +
-           ((int64_t)(iz + pt.gz) * pt.Y + (iy + pt.gy)) * pt.X + (ix + pt.gx);
+    dir = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+    return nb[dir] + ((int64_t)(iz + pt.gz) * pt.Y + (iy + pt.gy)) * pt.X + (ix + pt.gx);
+}
+__device__ __forceinline__ int64_t neighbour_source(const PatchDev& pt, const int64_t* __restrict__ nb, int ix,
+                                                    int iy, int iz) {
+    int dir;
+    return neighbour_source_dir(pt, nb, ix, iy, iz, dir);
 }
 
 // Geometry needed by the guard fill: box extent, boundary kinds and the owner map
